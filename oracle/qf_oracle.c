@@ -1,0 +1,396 @@
+/*
+ * qf_oracle.c -- plain CPU complex128 qudit state-vector simulator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle for the GPU
+ * library: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or helper with the
+ * CUDA path, and the CUDA path never calls it.
+ *
+ * Everything here is written straight from the definitions in the paper
+ * (QuForge, arXiv 2409.17716, Appendix B "Matrix form of the quantum gates"):
+ * every gate is built entry by entry from its formula, and every gate is applied
+ * by the same explicit gather / multiply / scatter loop over the groups of
+ * amplitudes it couples.  No blocking, fusion or reordering.
+ *
+ * Conventions (Appendix B, "Generalized CNOT gate", decimal representation):
+ *   basis index  j = sum_k j_k d^(n-1-k),  so qudit 0 is the most significant
+ *   digit and qudit q has stride d^(n-1-q).  Levels are 0-based, as the paper's
+ *   code uses them (end of "Generalized rotation gate").
+ *   A k-qudit matrix U acting on targets (t_0, ..., t_{k-1}) is indexed by the
+ *   row/column number r = sum_i r_i d^(k-1-i), r_i being the level of qudit t_i,
+ *   so t_0 is the most significant factor (the left factor of the Kronecker
+ *   product).  Matrices are row-major, complex128.
+ *
+ * Arithmetic is IEEE double, compiled with -ffp-contract=off so the x86 and Arm
+ * builds round identically.  Gate application is parallelised with OpenMP over
+ * independent groups only; every output amplitude is computed by the same
+ * sequence of operations as in a serial run.  Reductions are serial.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define OR_PI 3.14159265358979323846264338327950288
+
+static long long or_ipow(int d, int e)
+{
+    long long r = 1;
+    for (int i = 0; i < e; ++i) r *= d;
+    return r;
+}
+
+/* omega^m with omega = exp(2 pi i / d)  ("Generalized phase-shift gate").
+ * The exponent is reduced mod d first, which changes nothing mathematically. */
+static cplx or_omega_pow(int d, long long m)
+{
+    long long r = m % d;
+    if (r < 0) r += d;
+    double a = 2.0 * OR_PI * (double)r / (double)d;
+    return cos(a) + I * sin(a);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Single-qudit gate matrices (d x d, row-major).                            */
+/* ------------------------------------------------------------------------- */
+
+/* Identity. */
+void or_gate_identity(int d, cplx *U)
+{
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) U[a * d + b] = (a == b) ? 1.0 : 0.0;
+}
+
+/* Fourier / generalised Hadamard ("Fourier gate"): H_ab = omega^(a b) / sqrt(d). */
+void or_gate_fourier(int d, cplx *U)
+{
+    double s = 1.0 / sqrt((double)d);
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) U[a * d + b] = s * or_omega_pow(d, (long long)a * b);
+}
+
+/* Generalised NOT ("Generalized NOT gate"): X_s |x> = |x + s mod d>.
+ * Column x has its single 1 in row (x + s) mod d. */
+void or_gate_shift(int d, int s, cplx *U)
+{
+    for (int a = 0; a < d * d; ++a) U[a] = 0.0;
+    for (int x = 0; x < d; ++x) {
+        int y = (int)(((long long)x + s) % d);
+        if (y < 0) y += d;
+        U[y * d + x] = 1.0;
+    }
+}
+
+/* Phase-shift / clock ("Generalized phase-shift gate"): P = diag(1, w, ..., w^(d-1));
+ * this returns P^p = diag(w^(p k)). */
+void or_gate_clock(int d, int p, cplx *U)
+{
+    for (int a = 0; a < d * d; ++a) U[a] = 0.0;
+    for (int k = 0; k < d; ++k) U[k * d + k] = or_omega_pow(d, (long long)p * k);
+}
+
+/* Generators S of the rotations ("Generalized Gell-Mann matrices"), 0-based:
+ *   'x': S_x^{jk} = |j><k| + |k><j|
+ *   'y': S_y^{jk} = -i|j><k| + i|k><j|
+ *   'z': two-level diagonal |j><j| - |k><k|  (the level-pair RZ^{jk}; equals
+ *        S_z^1 of the paper when (j,k) = (0,1))
+ *   'g': Gell-Mann diagonal S_z^j, j = 1..d-1:
+ *        sqrt(2/(j(j+1))) (sum_{l<j} |l><l| - j |j><j|)   (0-based levels)
+ * Returns 0 on success, -1 on an invalid (axis, j, k). */
+int or_generator(int d, int j, int k, char axis, cplx *S)
+{
+    for (int a = 0; a < d * d; ++a) S[a] = 0.0;
+    if (axis == 'g') {
+        if (j < 1 || j > d - 1) return -1;
+        double c = sqrt(2.0 / ((double)j * (double)(j + 1)));
+        for (int l = 0; l < j; ++l) S[l * d + l] = c;
+        S[j * d + j] = -(double)j * c;
+        return 0;
+    }
+    if (j < 0 || k <= j || k >= d) return -1;
+    if (axis == 'x') {
+        S[j * d + k] = 1.0;
+        S[k * d + j] = 1.0;
+    } else if (axis == 'y') {
+        S[j * d + k] = -I;
+        S[k * d + j] = I;
+    } else if (axis == 'z') {
+        S[j * d + j] = 1.0;
+        S[k * d + k] = -1.0;
+    } else {
+        return -1;
+    }
+    return 0;
+}
+
+/* Rotation R(theta) = exp(-i theta S / 2) ("Generalized rotation gate").
+ * The non-zero elements are the ones the paper lists:
+ *   x: <j|R|j> = <k|R|k> = cos(theta/2), <j|R|k> = <k|R|j> = -i sin(theta/2)
+ *   y: <j|R|j> = <k|R|k> = cos(theta/2), <j|R|k> = -sin(theta/2), <k|R|j> = +sin(theta/2)
+ *   z/g: diagonal, <l|R|l> = exp(-i theta v_l / 2) with v_l the diagonal of S
+ *   all other levels: 1.
+ * Returns 0 on success, -1 on invalid arguments. */
+int or_gate_rot(int d, int j, int k, double theta, char axis, cplx *U)
+{
+    cplx *S = (cplx *)malloc(sizeof(cplx) * (size_t)d * d);
+    if (!S) return -1;
+    if (or_generator(d, j, k, axis, S) != 0) { free(S); return -1; }
+    or_gate_identity(d, U);
+    double c = cos(0.5 * theta), s = sin(0.5 * theta);
+    if (axis == 'x') {
+        U[j * d + j] = c;
+        U[k * d + k] = c;
+        U[j * d + k] = -I * s;
+        U[k * d + j] = -I * s;
+    } else if (axis == 'y') {
+        U[j * d + j] = c;
+        U[k * d + k] = c;
+        U[j * d + k] = -s;
+        U[k * d + j] = s;
+    } else { /* diagonal generators: 'z', 'g' */
+        for (int l = 0; l < d; ++l) {
+            double v = creal(S[l * d + l]);
+            double a = -0.5 * theta * v;
+            U[l * d + l] = cos(a) + I * sin(a);
+        }
+    }
+    free(S);
+    return 0;
+}
+
+/* Plain row-major complex matrix product C = A B (m x m). */
+static void or_matmul(int m, const cplx *A, const cplx *B, cplx *C)
+{
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) {
+            cplx acc = 0.0;
+            for (int t = 0; t < m; ++t) acc += A[r * m + t] * B[t * m + c];
+            C[r * m + c] = acc;
+        }
+}
+
+/* dR/dtheta for R = exp(-i theta S/2): (-i S / 2) R(theta). */
+int or_gate_rot_deriv(int d, int j, int k, double theta, char axis, cplx *dU)
+{
+    size_t sz = sizeof(cplx) * (size_t)d * d;
+    cplx *S = (cplx *)malloc(sz), *R = (cplx *)malloc(sz);
+    if (!S || !R) { free(S); free(R); return -1; }
+    if (or_generator(d, j, k, axis, S) != 0 || or_gate_rot(d, j, k, theta, axis, R) != 0) {
+        free(S); free(R); return -1;
+    }
+    for (int a = 0; a < d * d; ++a) S[a] *= -0.5 * I;
+    or_matmul(d, S, R, dU);
+    free(S); free(R);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Two-qudit gate matrices (d^2 x d^2, row-major, control = first factor).   */
+/* ------------------------------------------------------------------------- */
+
+/* Generalised CNOT = SUM ("Generalized CNOT gate"): |c>|t> -> |c>|t + c mod d>,
+ * i.e. <c, t (+) c| C_x |c, t> = 1.  The index rule of the paper is used; the
+ * displayed case equation there is garbled and is not followed. */
+void or_gate_sum(int d, cplx *U)
+{
+    int D2 = d * d;
+    for (int a = 0; a < D2 * D2; ++a) U[a] = 0.0;
+    for (int c = 0; c < d; ++c)
+        for (int t = 0; t < d; ++t) {
+            int col = c * d + t;
+            int row = c * d + (t + c) % d;
+            U[row * D2 + col] = 1.0;
+        }
+}
+
+/* Generalised SWAP ("Generalized SWAP Gate"): |x>|y> -> |y>|x>. */
+void or_gate_swap(int d, cplx *U)
+{
+    int D2 = d * d;
+    for (int a = 0; a < D2 * D2; ++a) U[a] = 0.0;
+    for (int x = 0; x < d; ++x)
+        for (int y = 0; y < d; ++y) U[(y * d + x) * D2 + (x * d + y)] = 1.0;
+}
+
+/* Controlled rotation ("Controlled Rotation Gate"):
+ *   C = sum_{m=0}^{d-1} |m><m| (x) R^{jk}_alpha(m theta).
+ * deriv != 0 returns dC/dtheta = sum_m |m><m| (x) m R'(m theta). */
+static int or_gate_crot_impl(int d, int j, int k, double theta, char axis, int deriv, cplx *U)
+{
+    int D2 = d * d;
+    cplx *R = (cplx *)malloc(sizeof(cplx) * (size_t)d * d);
+    if (!R) return -1;
+    for (int a = 0; a < D2 * D2; ++a) U[a] = 0.0;
+    for (int m = 0; m < d; ++m) {
+        int rc = deriv ? or_gate_rot_deriv(d, j, k, m * theta, axis, R)
+                       : or_gate_rot(d, j, k, m * theta, axis, R);
+        if (rc != 0) { free(R); return -1; }
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) {
+                cplx v = R[a * d + b];
+                if (deriv) v *= (double)m;
+                U[(m * d + a) * D2 + (m * d + b)] = v;
+            }
+    }
+    free(R);
+    return 0;
+}
+
+int or_gate_crot(int d, int j, int k, double theta, char axis, cplx *U)
+{
+    return or_gate_crot_impl(d, j, k, theta, axis, 0, U);
+}
+
+int or_gate_crot_deriv(int d, int j, int k, double theta, char axis, cplx *U)
+{
+    return or_gate_crot_impl(d, j, k, theta, axis, 1, U);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Gate application.                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* Applies the d^k x d^k matrix U to the target qudits of psi (length d^n):
+ *   psi'[.., r, ..] = sum_m U[r, m] psi[.., m, ..]
+ * for every assignment of the non-target digits.  Targets must be distinct
+ * and in [0, n).  Returns 0, or -1 on invalid arguments. */
+int or_apply(cplx *psi, int d, int n, const int *targets, int k, const cplx *U)
+{
+    if (d < 2 || n < 1 || k < 1 || k > n) return -1;
+    int is_target[64];
+    if (n > 64) return -1;
+    memset(is_target, 0, sizeof(is_target));
+    for (int i = 0; i < k; ++i) {
+        if (targets[i] < 0 || targets[i] >= n || is_target[targets[i]]) return -1;
+        is_target[targets[i]] = 1;
+    }
+    long long N = or_ipow(d, n);
+    long long K = or_ipow(d, k);
+    long long G = N / K;
+    long long *stride = (long long *)malloc(sizeof(long long) * n);
+    long long *off = (long long *)malloc(sizeof(long long) * K);
+    if (!stride || !off) { free(stride); free(off); return -1; }
+    for (int q = 0; q < n; ++q) stride[q] = or_ipow(d, n - 1 - q);
+    /* offset of row/column r inside a group: its digits r_i sit on qudit t_i */
+    for (long long r = 0; r < K; ++r) {
+        long long rem = r, o = 0;
+        for (int i = k - 1; i >= 0; --i) {
+            o += (rem % d) * stride[targets[i]];
+            rem /= d;
+        }
+        off[r] = o;
+    }
+    int fail = 0;
+#pragma omp parallel
+    {
+        cplx *v = (cplx *)malloc(sizeof(cplx) * K);
+        if (!v) {
+#pragma omp atomic write
+            fail = 1;
+        } else {
+#pragma omp for schedule(static)
+            for (long long g = 0; g < G; ++g) {
+                /* base index: the digits of g fill the non-target qudits,
+                 * least significant qudit first */
+                long long rem = g, base = 0;
+                for (int q = n - 1; q >= 0; --q) {
+                    if (is_target[q]) continue;
+                    base += (rem % d) * stride[q];
+                    rem /= d;
+                }
+                for (long long m = 0; m < K; ++m) v[m] = psi[base + off[m]];
+                for (long long r = 0; r < K; ++r) {
+                    cplx acc = 0.0;
+                    for (long long m = 0; m < K; ++m) acc += U[r * K + m] * v[m];
+                    psi[base + off[r]] = acc;
+                }
+            }
+            free(v);
+        }
+    }
+    free(stride);
+    free(off);
+    return fail ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Reductions (serial, plain summation in index order).                      */
+/* ------------------------------------------------------------------------- */
+
+/* Squared norm sum_i |psi_i|^2. */
+double or_norm2(const cplx *psi, long long N)
+{
+    double s = 0.0;
+    for (long long i = 0; i < N; ++i) s += creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+    return s;
+}
+
+/* <N_q> = sum_i i_q |psi_i|^2 for every qudit q, with N = diag(0, 1, ..., d-1)
+ * the level-number observable and i_q the q-th digit of i ("Generalized CNOT
+ * gate", decimal representation).  out has n entries. */
+void or_expect_number(const cplx *psi, int d, int n, double *out)
+{
+    long long N = or_ipow(d, n);
+    for (int q = 0; q < n; ++q) out[q] = 0.0;
+    for (long long i = 0; i < N; ++i) {
+        double p = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+        long long rem = i;
+        for (int q = n - 1; q >= 0; --q) {
+            out[q] += (double)(rem % d) * p;
+            rem /= d;
+        }
+    }
+}
+
+/* <psi| O_q |psi> for a d x d matrix O on qudit q (complex result; real for
+ * Hermitian O). */
+void or_expect_obs(const cplx *psi, int d, int n, int q, const cplx *O, double *out_re, double *out_im)
+{
+    long long N = or_ipow(d, n);
+    long long S = or_ipow(d, n - 1 - q);
+    cplx acc = 0.0;
+    for (long long i = 0; i < N; ++i) {
+        long long l = (i / S) % d;
+        long long base = i - l * S;
+        cplx row = 0.0;
+        for (int m = 0; m < d; ++m) row += O[l * d + m] * psi[base + m * S];
+        acc += conj(psi[i]) * row;
+    }
+    *out_re = creal(acc);
+    *out_im = cimag(acc);
+}
+
+/* Marginal probabilities of the qudits listed in idx (k of them):
+ * out[r] = sum over i whose digits on idx[0..k-1] spell r (idx[0] most
+ * significant) of |psi_i|^2.  out has d^k entries. */
+void or_marginal(const cplx *psi, int d, int n, const int *idx, int k, double *out)
+{
+    long long N = or_ipow(d, n);
+    long long K = or_ipow(d, k);
+    for (long long r = 0; r < K; ++r) out[r] = 0.0;
+    for (long long i = 0; i < N; ++i) {
+        double p = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+        long long r = 0;
+        for (int a = 0; a < k; ++a) r = r * d + (i / or_ipow(d, n - 1 - idx[a])) % d;
+        out[r] += p;
+    }
+}
+
+/* <a|b> = sum_i conj(a_i) b_i. */
+void or_inner(const cplx *a, const cplx *b, long long N, double *out_re, double *out_im)
+{
+    cplx acc = 0.0;
+    for (long long i = 0; i < N; ++i) acc += conj(a[i]) * b[i];
+    *out_re = creal(acc);
+    *out_im = cimag(acc);
+}
+
+/* psi = |index>  (the basis state whose decimal representation is index). */
+void or_basis_state(cplx *psi, long long N, long long index)
+{
+    for (long long i = 0; i < N; ++i) psi[i] = 0.0;
+    psi[index] = 1.0;
+}
