@@ -1,0 +1,227 @@
+/*
+ * qf.h -- C ABI of libqf, a GB300 (sm_103a) qudit state-vector engine.
+ *
+ * The operations follow QuForge (arXiv 2409.17716): a register of n qudits of
+ * dimension d is a dense complex vector of d^n amplitudes (section "Library
+ * Architecture"; the State class), gates from Appendix B "Matrix form of the
+ * quantum gates" are applied to it in circuit order (the Circuit class), and
+ * the result is reduced to expectation values (the measure utility of
+ * section "Code style" returns the marginal probabilities they are built from).
+ *
+ * Conventions shared by every entry point
+ *   - Basis index i = sum_q i_q d^(n-1-q) (Appendix B, "Generalized CNOT
+ *     gate", decimal representation): qudit 0 is the most significant digit,
+ *     qudit q has stride d^(n-1-q).  Levels are 0-based.
+ *   - Amplitudes are stored contiguously, real and imaginary parts
+ *     interleaved: QF_C64 = two floats per amplitude, QF_C128 = two doubles.
+ *     Device buffers must be 16-byte aligned.
+ *   - Every call is asynchronous on the state's CUDA stream, except the ones
+ *     documented as returning host results (they synchronise that stream).
+ *   - Arguments are validated on the host before any launch; an invalid call
+ *     returns QF_ERR_ARG and leaves the state untouched.  qf_last_error()
+ *     returns a thread-local message describing the most recent failure.
+ *   - Angles and matrices are passed in FP64 on the host.  Gate entries are
+ *     computed in FP64 once per gate and rounded to the state's precision.
+ *   - Supported sizes: 2 <= d <= 16, n >= 1, d^n amplitudes must fit in
+ *     device memory (QF_ERR_OOM otherwise).
+ */
+#ifndef QF_H
+#define QF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QF_OK = 0,
+    QF_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+    QF_ERR_OOM = 2,         /* device or pinned-host allocation failed */
+    QF_ERR_CUDA = 3,        /* a CUDA runtime call failed (message in qf_last_error) */
+    QF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    QF_ERR_UNSUPPORTED = 5  /* valid request outside this build's limits */
+} qf_status;
+
+typedef enum { QF_C64 = 0, QF_C128 = 1 } qf_dtype;
+
+typedef struct qf_state qf_state;
+typedef struct qf_program qf_program;
+
+/* Observables for qf_expect (section "Code style": measure returns the
+ * probabilities of the measured qudits; <N_q> = sum_m m P_q(m)).
+ *   QF_OBS_NUMBER_ALL : out[0..n-1] = <N_q> for N = diag(0, 1, ..., d-1) on
+ *                       every qudit q, out[n] = sum_i |psi_i|^2.  (n+1 values)
+ *   QF_OBS_NORM       : out[0] = sum_i |psi_i|^2.                  (1 value)
+ *   QF_OBS_HERMITIAN  : out[0] = Re <psi| O_q |psi>, out[1] = Im, for the
+ *                       d x d row-major complex matrix `matrix` (interleaved
+ *                       re, im, FP64, host memory) on qudit `q`. (2 values)
+ *   QF_OBS_MARGINAL   : out[r] = probability that qudit `q` is at level r,
+ *                       r = 0..d-1.                                 (d values)
+ * All sums are accumulated in FP64 on the device. */
+typedef enum { QF_OBS_NUMBER_ALL = 0, QF_OBS_NORM = 1, QF_OBS_HERMITIAN = 2, QF_OBS_MARGINAL = 3 } qf_obs_kind;
+
+typedef struct {
+    int kind;              /* qf_obs_kind */
+    int q;                 /* qudit for QF_OBS_HERMITIAN / QF_OBS_MARGINAL */
+    const double *matrix;  /* QF_OBS_HERMITIAN: host FP64 interleaved d x d */
+} qf_obs;
+
+/* Thread-local description of the last error (never NULL). */
+const char *qf_last_error(void);
+
+/* Number of output doubles qf_expect writes for `obs` on a (d, n) register,
+ * or -1 for an invalid observable. */
+int qf_expect_size(int d, int n, const qf_obs *obs);
+
+/* ---------------------------------------------------------------- states */
+
+/* Allocates a state of d^n amplitudes on the current CUDA device, owned by the
+ * library, and sets it to |0...0> (the State class with an all-zero string).
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  The handle
+ * is written to *out.  Errors: QF_ERR_ARG (d, n out of range, out NULL),
+ * QF_ERR_OOM, QF_ERR_CUDA. */
+qf_status qf_state_init(int d, int n, qf_dtype dt, void *cuda_stream, qf_state **out);
+
+/* Wraps caller-owned device memory (e.g. a torch tensor's data pointer) of
+ * d^n amplitudes of type dt.  The memory is borrowed: qf_state_free does not
+ * free it, and it must outlive the handle.  Contents are left unchanged.
+ * Errors: QF_ERR_ARG (NULL or misaligned pointer, bad sizes). */
+qf_status qf_state_wrap(int d, int n, qf_dtype dt, void *dev_ptr, void *cuda_stream, qf_state **out);
+
+/* Releases the handle, its scratch buffers and, if owned, the amplitudes.
+ * Synchronises the state's stream first.  NULL is accepted. */
+qf_status qf_state_free(qf_state *s);
+
+/* Device pointer of the amplitudes and their count d^n. */
+qf_status qf_state_ptr(qf_state *s, void **dev_ptr, long long *num_amps);
+
+/* Shape of a state: qudit dimension, qudit count and dtype (any output
+ * pointer may be NULL). */
+qf_status qf_state_info(const qf_state *s, int *d, int *n, qf_dtype *dt);
+
+/* Changes the stream subsequent calls on this state are issued on. */
+qf_status qf_state_set_stream(qf_state *s, void *cuda_stream);
+
+/* psi = |index> for 0 <= index < d^n (State('i_0-i_1-...') of "Code style"
+ * with the digits of `index`).  Writes every amplitude. */
+qf_status qf_state_set_basis(qf_state *s, long long index);
+
+/* dst <- src (same d, n, dtype); both on dst's stream. */
+qf_status qf_state_copy(qf_state *dst, const qf_state *src);
+
+/* ---------------------------------------------------------------- gates */
+
+/* Custom gate (section "Quantum Gates": users may supply a matrix; the
+ * Grover example applies 9 x 9 matrices on two qutrits).  U is a host
+ * row-major d^k x d^k complex matrix (interleaved re, im, FP64), copied at
+ * the call; targets[0] is the most significant factor.  Targets must be
+ * distinct and in [0, n); 1 <= k and d^k <= 64.  U is not checked for
+ * unitarity.  One pass over the touched amplitudes. */
+qf_status qf_apply_gate(qf_state *s, const int *targets, int k, const double *U);
+
+/* Rotation R(theta) = exp(-i theta S / 2) on qudit q (Appendix B,
+ * "Generalized rotation gate"), with S chosen by axis:
+ *   'x' : S_x^{jk} = |j><k| + |k><j|        (0 <= j < k < d)
+ *   'y' : S_y^{jk} = -i|j><k| + i|k><j|     (0 <= j < k < d)
+ *   'z' : |j><j| - |k><k|, the level-pair RZ that phases only j and k
+ *         (0 <= j < k < d; equals the paper's S_z^1 for (j, k) = (0, 1))
+ *   'g' : Gell-Mann diagonal S_z^j, 1 <= j <= d-1, k ignored
+ *         (sqrt(2/(j(j+1))) on levels 0..j-1, -j sqrt(2/(j(j+1))) on level j).
+ * Only the levels the rotation moves are read and written. */
+qf_status qf_apply_rot(qf_state *s, int q, int j, int k, double theta, char axis);
+
+/* Controlled rotation (Appendix B, "Controlled Rotation Gate"):
+ * sum_m |m><m|_c (x) R^{jk}_axis(m theta)_t; control level m scales the angle,
+ * m = 0 is the identity.  c != t, axis and levels as in qf_apply_rot. */
+qf_status qf_apply_crot(qf_state *s, int c, int t, int j, int k, double theta, char axis);
+
+/* Generalised CNOT / SUM (Appendix B, "Generalized CNOT gate"):
+ * |..i_c..i_t..> -> |..i_c..(i_t + i_c) mod d..>, for c < t and c > t. */
+qf_status qf_apply_sum(qf_state *s, int c, int t);
+
+/* Generalised SWAP (Appendix B, "Generalized SWAP Gate") of qudits a != b. */
+qf_status qf_apply_swap(qf_state *s, int a, int b);
+
+/* Generalised NOT X_s (Appendix B, "Generalized NOT gate"):
+ * |x> -> |x + shift mod d> on qudit q (any integer shift). */
+qf_status qf_apply_x(qf_state *s, int q, int shift);
+
+/* Phase-shift / clock gate to a power (Appendix B, "Generalized phase-shift
+ * gate"): |x> -> w^(power x) |x>, w = exp(2 pi i / d). */
+qf_status qf_apply_z(qf_state *s, int q, int power);
+
+/* Fourier / generalised Hadamard (Appendix B, "Fourier gate"):
+ * H_ab = w^(a b) / sqrt(d). */
+qf_status qf_apply_h(qf_state *s, int q);
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Evaluates `obs` (see qf_obs) and writes qf_expect_size() doubles to host
+ * memory out_host.  Synchronises the state's stream. */
+qf_status qf_expect(qf_state *s, const qf_obs *obs, double *out_host);
+
+/* As qf_expect, but writes the FP64 results to device memory out_dev
+ * (8-byte aligned) asynchronously on the state's stream. */
+qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev);
+
+/* ---------------------------------------------------------------- programs
+ * A program is a circuit recorded once (the Circuit class of "Library
+ * Architecture") and executed many times.  Running it plans passes: runs of
+ * gates whose qudits fit one on-chip tile are applied in a single read and
+ * write of the state (gates on disjoint qudits are moved past each other only
+ * where they commute).  Rotations may take their angle from a parameter
+ * vector supplied at run time (param_slot >= 0) or keep a fixed angle
+ * (param_slot < 0, angle = theta). */
+
+qf_status qf_program_create(int d, int n, qf_program **out);
+qf_status qf_program_free(qf_program *p);
+/* Number of gates recorded, and the number of parameter slots referenced
+ * (1 + largest slot, 0 if none). */
+qf_status qf_program_info(const qf_program *p, int *num_gates, int *num_params);
+
+qf_status qf_program_add_gate(qf_program *p, const int *targets, int k, const double *U);
+qf_status qf_program_add_rot(qf_program *p, int q, int j, int k, char axis, int param_slot, double theta);
+qf_status qf_program_add_crot(qf_program *p, int c, int t, int j, int k, char axis, int param_slot, double theta);
+qf_status qf_program_add_sum(qf_program *p, int c, int t);
+qf_status qf_program_add_swap(qf_program *p, int a, int b);
+qf_status qf_program_add_x(qf_program *p, int q, int shift);
+qf_status qf_program_add_z(qf_program *p, int q, int power);
+qf_status qf_program_add_h(qf_program *p, int q);
+
+/* Fusion control: enable != 0 (the default) plans fused passes; enable = 0
+ * gives one pass per gate, in recorded order (the per-gate kernels).  Takes
+ * effect at the next run. */
+qf_status qf_program_set_fusion(qf_program *p, int enable);
+
+/* Applies the program to s (same d and n).  params: host FP64 vector of
+ * at least num_params entries (may be NULL if num_params == 0).  Async. */
+qf_status qf_program_run(qf_program *p, qf_state *s, const double *params);
+
+/* Number of kernel passes the last run or adjoint launched (for throughput
+ * accounting), or -1 before the first run. */
+int qf_program_last_passes(const qf_program *p);
+
+/* Per-pass timing (tracing).  With timing enabled, every run records a CUDA
+ * event on the state's stream before its first pass and after each pass;
+ * the records accumulate over runs until qf_program_pass_times reads them.
+ * Enabling or disabling clears them. */
+qf_status qf_program_set_timing(qf_program *p, int enable);
+
+/* Waits for the last timed run, then writes, for each of the first `max`
+ * passes timed since the last read (all runs, in launch order), the elapsed
+ * milliseconds between its events, its kernel (0 = tile pass, 1 = strided
+ * single-gate pass) and its algorithmic HBM bytes (amplitudes read plus
+ * written: 2 N b for a tile pass, the touched rows for a strided pass);
+ * *count = number of passes timed.  Clears the records.  Any output pointer
+ * may be NULL. */
+qf_status qf_program_pass_times(qf_program *p, int max, float *ms, int *kind, double *bytes, int *count);
+
+/* Plans the program for states of dtype dt without running it (host only):
+ * number of passes, how many of them are single gates on the strided kernel,
+ * and the largest number of ops in one pass.  Output pointers may be NULL. */
+qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_strided, int *max_ops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QF_H */

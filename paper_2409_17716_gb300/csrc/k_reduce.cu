@@ -1,0 +1,299 @@
+// k_reduce.cu -- state initialisation and FP64 reductions.
+//
+// Expectation of the level-number observable on every qudit in one pass:
+//   <N_q> = sum_i i_q |psi_i|^2,   i = sum_q i_q d^(n-1-q)
+// (the measure utility of section "Code style" returns the marginals
+// P_q(m) this is built from: <N_q> = sum_m m P_q(m)).
+//
+// The state is cut into chunks of d^rc contiguous amplitudes, rc = a + B.  A
+// CTA has exactly d^a threads and thread t reads amplitudes t + d^a u of a
+// chunk (coalesced), so
+//   * the lowest a digits of every amplitude a thread reads are the digits of
+//     t: their contribution is digit_r(t) * (thread mass), taken once at the
+//     end;
+//   * the next B digits are the digits of the unrolled loop counter u: their
+//     weights are compile-time constants;
+//   * the digits above rc are constant over a chunk: the CTA reduces the chunk
+//     mass once and adds digit_q(chunk) * mass to an FP64 accumulator per q.
+// Per amplitude this costs |psi|^2, one add and at most B fused multiply-adds
+// (complex64 states accumulate a chunk in FP32, ~d^B terms per thread, then
+// everything is summed in FP64).  CTA partials go to a scratch array that a
+// second one-CTA kernel sums in a fixed order, so results are deterministic.
+#include "qf_internal.cuh"
+
+namespace qf {
+
+// ------------------------------------------------------------------ init
+template <typename R>
+__global__ void k_fill_basis(cplx<R> *psi, long long N, long long index) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (; i < N; i += stride) psi[i] = mk<R>(i == index ? (R)1 : (R)0, (R)0);
+}
+
+template <typename R>
+cudaError_t launch_basis(const Launch &L, cplx<R> *psi, long long N, long long index) {
+    long long blocks = (N + 255) / 256;
+    long long cap = (long long)L.num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_fill_basis<R><<<(unsigned)blocks, 256, 0, L.stream>>>(psi, N, index);
+    return cudaGetLastError();
+}
+template cudaError_t launch_basis<float>(const Launch &, cplx<float> *, long long, long long);
+template cudaError_t launch_basis<double>(const Launch &, cplx<double> *, long long, long long);
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide FP64 sum; result valid in every thread.  `red` has >= 33 slots.
+__device__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < nw ? red[lane] : 0.0;
+        s = warp_sum(s);
+        if (lane == 0) red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <int D> struct NumCfg;
+template <> struct NumCfg<2> { static constexpr int A = 8, B = 5; };
+template <> struct NumCfg<3> { static constexpr int A = 5, B = 3; };
+template <> struct NumCfg<4> { static constexpr int A = 4, B = 2; };
+template <> struct NumCfg<5> { static constexpr int A = 3, B = 2; };
+template <> struct NumCfg<6> { static constexpr int A = 3, B = 2; };
+template <> struct NumCfg<7> { static constexpr int A = 3, B = 1; };
+template <> struct NumCfg<8> { static constexpr int A = 3, B = 1; };
+
+constexpr int ipow_c(int d, int e) { return e == 0 ? 1 : d * ipow_c(d, e - 1); }
+
+// partials: gridDim.x rows of (n + 1) doubles: <N_q> for q < n, then norm.
+template <typename R, int D>
+__global__ void __launch_bounds__(ipow_c(D, NumCfg<D>::A)) k_expect_number(const cplx<R> *__restrict__ psi, int n,
+                                                                          long long nchunks, double *partials) {
+    constexpr int A = NumCfg<D>::A, B = NumCfg<D>::B;
+    constexpr int BLK = ipow_c(D, A);
+    constexpr int U = ipow_c(D, B);
+    constexpr int CH = BLK * U;
+    using Acc = R;  // FP32 within a chunk for complex64, FP64 for complex128
+    __shared__ double red[33];
+    __shared__ double hacc[kMaxQudits + 1];
+    const int tid = threadIdx.x;
+    const int nh = n - A - B;  // digits constant over a chunk
+    for (int q = tid; q <= kMaxQudits; q += BLK) hacc[q] = 0.0;
+
+    double mass = 0.0;
+    double w[B];
+#pragma unroll
+    for (int r = 0; r < B; ++r) w[r] = 0.0;
+
+    for (long long c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const cplx<R> *p = psi + c * CH + tid;
+        Acc m = 0, wl[B];
+#pragma unroll
+        for (int r = 0; r < B; ++r) wl[r] = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            cplx<R> v = p[u * BLK];
+            Acc pr = v.x * v.x + v.y * v.y;
+            m += pr;
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+                int pw = 1;
+#pragma unroll
+                for (int s = 0; s < r; ++s) pw *= D;
+                const int dig = (u / pw) % D;
+                if (dig) wl[r] += (Acc)dig * pr;
+            }
+        }
+        mass += (double)m;
+#pragma unroll
+        for (int r = 0; r < B; ++r) w[r] += (double)wl[r];
+        if (nh > 0) {
+            double cm = block_sum((double)m, red);
+            // digits of the chunk index are the digits of qudits nh-1 ... 0
+            if (tid < nh) {
+                // qudit tid's digit of the chunk index: divide by d^(nh-1-tid)
+                long long div = 1;
+                for (int s = 0; s < nh - 1 - tid; ++s) div *= D;
+                const int dig = (int)((c / div) % D);
+                hacc[tid] += (double)dig * cm;
+            }
+        }
+    }
+    __syncthreads();
+    // per-qudit totals of this CTA
+    double *out = partials + (long long)blockIdx.x * (n + 1);
+    // thread-constant digits: qudit n-1-r for r < A
+    int t = tid;
+    for (int r = 0; r < A; ++r) {
+        const int dig = t % D;
+        t /= D;
+        double s = block_sum((double)dig * mass, red);
+        if (tid == 0 && n - 1 - r >= 0) out[n - 1 - r] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < B; ++r) {
+        double s = block_sum(w[r], red);
+        if (tid == 0) out[n - 1 - A - r] = s;
+    }
+    double s = block_sum(mass, red);
+    if (tid == 0) out[n] = s;
+    for (int q = tid; q < nh; q += BLK) out[q] = hacc[q];
+}
+
+// Generic path (runtime d, or registers too small for the chunked kernel):
+// each thread extracts every digit of every amplitude.  FP64 throughout.
+template <typename R>
+__global__ void __launch_bounds__(256) k_expect_number_generic(const cplx<R> *__restrict__ psi, int d, int n, long long N,
+                                                                double *partials) {
+    __shared__ double red[33];
+    double acc[kMaxQudits + 1];
+    for (int q = 0; q <= n; ++q) acc[q] = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        cplx<R> v = psi[i];
+        double p = (double)v.x * v.x + (double)v.y * v.y;
+        acc[n] += p;
+        long long rem = i;
+        for (int q = n - 1; q >= 0; --q) {
+            long long nx = rem / d;
+            acc[q] += (double)(rem - nx * d) * p;
+            rem = nx;
+        }
+    }
+    double *out = partials + (long long)blockIdx.x * (n + 1);
+    for (int q = 0; q <= n; ++q) {
+        double s = block_sum(acc[q], red);
+        if (threadIdx.x == 0) out[q] = s;
+    }
+}
+
+// Sums `rows` rows of `cols` partials in row order.
+__global__ void k_sum_partials(const double *partials, int rows, int cols, double *out) {
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < rows; ++r) s += partials[(long long)r * cols + c];
+        out[c] = s;
+    }
+}
+
+// Fibre reduction over target qudit q (stride S): kind 0 = marginal P_q(m)
+// (d outputs), kind 1 = <psi|O_q|psi> (2 outputs: re, im) with O in `obs`.
+template <typename R>
+__global__ void __launch_bounds__(256) k_fibre_reduce(const cplx<R> *__restrict__ psi, int d, long long nfib, long long S,
+                                                        int kind, const double2 *obs, double *partials) {
+    __shared__ double red[33];
+    double acc[kMaxD];
+    for (int m = 0; m < d; ++m) acc[m] = 0.0;
+    double are = 0.0, aim = 0.0;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nfib; f += (long long)gridDim.x * blockDim.x) {
+        long long h = f / S, lo = f - h * S;
+        const cplx<R> *p = psi + h * d * S + lo;
+        if (kind == 0) {
+            for (int m = 0; m < d; ++m) {
+                cplx<R> v = p[m * S];
+                acc[m] += (double)v.x * v.x + (double)v.y * v.y;
+            }
+        } else {
+            double vr[kMaxD], vi[kMaxD];
+            for (int m = 0; m < d; ++m) { cplx<R> v = p[m * S]; vr[m] = v.x; vi[m] = v.y; }
+            for (int l = 0; l < d; ++l) {
+                double rr = 0.0, ri = 0.0;
+                for (int m = 0; m < d; ++m) {
+                    double2 o = obs[l * d + m];
+                    rr += o.x * vr[m] - o.y * vi[m];
+                    ri += o.x * vi[m] + o.y * vr[m];
+                }
+                // conj(v_l) * (O v)_l
+                are += vr[l] * rr + vi[l] * ri;
+                aim += vr[l] * ri - vi[l] * rr;
+            }
+        }
+    }
+    const int cols = kind == 0 ? d : 2;
+    double *out = partials + (long long)blockIdx.x * cols;
+    if (kind == 0) {
+        for (int m = 0; m < d; ++m) {
+            double s = block_sum(acc[m], red);
+            if (threadIdx.x == 0) out[m] = s;
+        }
+    } else {
+        double s0 = block_sum(are, red);
+        double s1 = block_sum(aim, red);
+        if (threadIdx.x == 0) { out[0] = s0; out[1] = s1; }
+    }
+}
+
+// Upper bound on the CTAs the reductions use (scratch rows).
+int reduce_max_blocks(int num_sms) { return 2 * num_sms; }
+
+// <N_q> for every q plus the norm -> out_dev[0..n].  `partials` must hold
+// reduce_max_blocks() * (n + 1) doubles.
+template <typename R>
+cudaError_t launch_expect_number(const Launch &L, const cplx<R> *psi, int d, int n, double *partials, double *out_dev) {
+    long long N = 1;
+    for (int i = 0; i < n; ++i) N *= d;
+    int maxb = reduce_max_blocks(L.num_sms);
+    int blocks = 0;
+    switch (d) {
+#define QF_CASE(DD)                                                                                  \
+    case DD: {                                                                                       \
+        constexpr int CH = ipow_c(DD, NumCfg<DD>::A + NumCfg<DD>::B);                                \
+        if (n >= NumCfg<DD>::A + NumCfg<DD>::B) {                                                    \
+            long long nch = N / CH;                                                                  \
+            blocks = (int)(nch < maxb ? nch : maxb);                                                 \
+            k_expect_number<R, DD><<<blocks, ipow_c(DD, NumCfg<DD>::A), 0, L.stream>>>(psi, n, nch, partials); \
+        }                                                                                            \
+        break;                                                                                       \
+    }
+        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
+#undef QF_CASE
+    default:
+        break;
+    }
+    if (blocks == 0) {
+        long long b = (N + 255) / 256;
+        blocks = (int)(b < maxb ? b : maxb);
+        k_expect_number_generic<R><<<blocks, 256, 0, L.stream>>>(psi, d, n, N, partials);
+    }
+    k_sum_partials<<<1, 64, 0, L.stream>>>(partials, blocks, n + 1, out_dev);
+    return cudaGetLastError();
+}
+
+// kind 0: marginal of qudit q (d outputs); kind 1: <O_q> (re, im); obs_dev
+// holds the d x d FP64 matrix for kind 1.
+template <typename R>
+cudaError_t launch_fibre_reduce(const Launch &L, const cplx<R> *psi, int d, int n, int q, int kind, const double2 *obs_dev,
+                                double *partials, double *out_dev) {
+    long long S = 1, N = 1;
+    for (int i = 0; i < n - 1 - q; ++i) S *= d;
+    for (int i = 0; i < n; ++i) N *= d;
+    long long nfib = N / d;
+    int maxb = reduce_max_blocks(L.num_sms);
+    long long b = (nfib + 255) / 256;
+    int blocks = (int)(b < maxb ? b : maxb);
+    k_fibre_reduce<R><<<blocks, 256, 0, L.stream>>>(psi, d, nfib, S, kind, obs_dev, partials);
+    k_sum_partials<<<1, 32, 0, L.stream>>>(partials, blocks, kind == 0 ? d : 2, out_dev);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_expect_number<float>(const Launch &, const cplx<float> *, int, int, double *, double *);
+template cudaError_t launch_expect_number<double>(const Launch &, const cplx<double> *, int, int, double *, double *);
+template cudaError_t launch_fibre_reduce<float>(const Launch &, const cplx<float> *, int, int, int, int, const double2 *,
+                                                double *, double *);
+template cudaError_t launch_fibre_reduce<double>(const Launch &, const cplx<double> *, int, int, int, int, const double2 *,
+                                                 double *, double *);
+
+}  // namespace qf

@@ -1,0 +1,411 @@
+// qf_gates.cu -- gate entries (FP64, host) and the pass planner.
+//
+// Gate entries follow Appendix B of the paper:
+//   Fourier            H_ab = w^(a b) / sqrt(d),  w = exp(2 pi i / d)
+//   generalised NOT    X_s |x> = |x + s mod d>
+//   phase-shift        P = diag(w^l), applied to a power p
+//   rotations          R = exp(-i theta S / 2) with S a generalised Gell-Mann
+//                      matrix: on levels (j, k)
+//                        x: [[c, -i s], [-i s, c]]   y: [[c, -s], [s, c]]
+//                      c = cos(theta/2), s = sin(theta/2); the level-pair
+//                      diagonal 'z' phases j by exp(-i theta/2), k by
+//                      exp(+i theta/2); the Gell-Mann diagonal 'g' (index j)
+//                      phases level l by exp(-i theta v_l / 2), v_l =
+//                      sqrt(2/(j(j+1))) for l < j, -j sqrt(2/(j(j+1))) for l = j
+//   controlled rot.    sum_m |m><m|_c (x) R(m theta)_t
+//   generalised CNOT   |c>|t> -> |c>|t + c mod d>
+//   SWAP               |x>|y> -> |y>|x>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "qf_host.h"
+
+namespace qf {
+
+long long ipow_ll(int d, int e) {
+    long long r = 1;
+    for (int i = 0; i < e; ++i) r *= d;
+    return r;
+}
+
+static cd omega_pow(int d, long long m) {
+    long long r = m % d;
+    if (r < 0) r += d;
+    double a = 2.0 * M_PI * (double)r / (double)d;
+    return cd(std::cos(a), std::sin(a));
+}
+
+qf_status check_gate(const HGate &g, int d, int n) {
+    auto bad = [&](const std::string &m) { return set_error(QF_ERR_ARG, m); };
+    if (g.nq < 1 || g.nq > 6) return bad("gate needs 1..6 qudits");
+    for (int i = 0; i < g.nq; ++i) {
+        if (g.q[i] < 0 || g.q[i] >= n) return bad("qudit index out of range [0, n)");
+        for (int k = 0; k < i; ++k)
+            if (g.q[k] == g.q[i]) return bad("qudits of a gate must be distinct");
+    }
+    switch (g.kind) {
+    case G_DENSE: {
+        long long K = ipow_ll(d, g.nq);
+        if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: d^k must be <= 64");
+        if ((long long)g.U.size() != K * K) return bad("custom gate matrix has the wrong size");
+        return QF_OK;
+    }
+    case G_ROT:
+    case G_CROT:
+        if ((g.kind == G_ROT) != (g.nq == 1)) return bad("rotation arity");
+        if (g.axis == 'g') {
+            if (g.j < 1 || g.j > d - 1) return bad("Gell-Mann diagonal index j must be in [1, d-1]");
+        } else if (g.axis == 'x' || g.axis == 'y' || g.axis == 'z') {
+            if (!(0 <= g.j && g.j < g.k && g.k < d)) return bad("levels must satisfy 0 <= j < k < d");
+        } else {
+            return bad("axis must be 'x', 'y', 'z' or 'g'");
+        }
+        if (!std::isfinite(g.theta)) return bad("angle is not finite");
+        return QF_OK;
+    case G_SUM:
+    case G_SWAP:
+        if (g.nq != 2) return bad("two-qudit gate needs two distinct qudits");
+        return QF_OK;
+    case G_X:
+    case G_Z:
+    case G_H:
+        if (g.nq != 1) return bad("single-qudit gate arity");
+        return QF_OK;
+    default:
+        return bad("unknown gate kind");
+    }
+}
+
+bool gate_is_param(const HGate &g) { return (g.kind == G_ROT || g.kind == G_CROT) && g.slot >= 0; }
+
+double gate_angle(const HGate &g, const double *params) {
+    if (g.slot >= 0 && params) return params[g.slot];
+    return g.theta;
+}
+
+// Rotation entries: PAIR layout (jj, jk, kj, kk) for x/y, diagonal (d) for z/g.
+static void rot_entries(int d, int j, int k, char axis, double th, cd *out, int *mask) {
+    const double c = std::cos(0.5 * th), s = std::sin(0.5 * th);
+    if (axis == 'x') {
+        out[0] = cd(c, 0); out[1] = cd(0, -s); out[2] = cd(0, -s); out[3] = cd(c, 0);
+        *mask = 0;
+        return;
+    }
+    if (axis == 'y') {
+        out[0] = cd(c, 0); out[1] = cd(-s, 0); out[2] = cd(s, 0); out[3] = cd(c, 0);
+        *mask = 0;
+        return;
+    }
+    for (int l = 0; l < d; ++l) out[l] = cd(1, 0);
+    if (axis == 'z') {
+        out[j] = cd(c, -s);
+        out[k] = cd(c, s);
+        *mask = (1 << j) | (1 << k);
+        return;
+    }
+    // 'g': Gell-Mann diagonal S_z^j
+    const double gam = std::sqrt(2.0 / ((double)j * (double)(j + 1)));
+    int msk = 0;
+    for (int l = 0; l <= j; ++l) {
+        const double v = (l < j) ? gam : -(double)j * gam;
+        const double a = -0.5 * th * v;
+        out[l] = cd(std::cos(a), std::sin(a));
+        msk |= 1 << l;
+    }
+    *mask = msk;
+}
+
+ROp resolve_gate(const HGate &g, int d, double th) {
+    ROp r;
+    std::memset(&r.op, 0, sizeof(TOp));
+    TOp &o = r.op;
+    o.a = g.q[0];
+    switch (g.kind) {
+    case G_H:
+        o.kind = OP_DENSE;
+        r.m.resize((size_t)d * d);
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) r.m[a * d + b] = omega_pow(d, (long long)a * b) / std::sqrt((double)d);
+        break;
+    case G_X: {
+        o.kind = OP_SHIFT;
+        int s = g.power % d;
+        if (s < 0) s += d;
+        o.s = s;
+        break;
+    }
+    case G_Z: {
+        o.kind = OP_DIAG;
+        r.m.resize(d);
+        int msk = 0;
+        for (int l = 0; l < d; ++l) {
+            long long e = ((long long)g.power * l) % d;
+            if (e < 0) e += d;
+            r.m[l] = omega_pow(d, e);
+            if (e != 0) msk |= 1 << l;
+        }
+        o.mask = msk;
+        break;
+    }
+    case G_ROT: {
+        o.j = g.j;
+        o.k = g.k;
+        if (g.axis == 'x' || g.axis == 'y') {
+            o.kind = OP_PAIR;
+            r.m.resize(4);
+        } else {
+            o.kind = OP_DIAG;
+            r.m.resize(d);
+        }
+        rot_entries(d, g.j, g.k, g.axis, th, r.m.data(), &o.mask);
+        break;
+    }
+    case G_CROT: {
+        o.c = g.q[0];
+        o.a = g.q[1];
+        o.j = g.j;
+        o.k = g.k;
+        const bool pair = g.axis == 'x' || g.axis == 'y';
+        o.kind = pair ? OP_CPAIR : OP_CDIAG;
+        const int per = pair ? 4 : d;
+        r.m.resize((size_t)per * d);
+        for (int m = 0; m < d; ++m) rot_entries(d, g.j, g.k, g.axis, m * th, r.m.data() + per * m, &o.mask);
+        break;
+    }
+    case G_SUM:
+        o.kind = OP_CSHIFT;
+        o.c = g.q[0];
+        o.a = g.q[1];
+        o.s = 1;
+        break;
+    case G_SWAP:
+        o.kind = OP_SWAP;
+        o.a = g.q[0];
+        o.c = g.q[1];
+        break;
+    case G_DENSE:
+        if (g.nq == 1) {
+            o.kind = OP_DENSE;
+        } else {
+            o.kind = OP_DENSEK;
+            o.nq = g.nq;
+            for (int i = 0; i < g.nq; ++i) o.q[i] = g.q[i];
+        }
+        r.m = g.U;
+        break;
+    }
+    return r;
+}
+
+std::vector<cd> dense_of(const ROp &r, int d) {
+    std::vector<cd> M((size_t)d * d, cd(0, 0));
+    const TOp &o = r.op;
+    switch (o.kind) {
+    case OP_DENSE:
+        M = r.m;
+        break;
+    case OP_PAIR:
+        for (int l = 0; l < d; ++l) M[l * d + l] = 1;
+        M[o.j * d + o.j] = r.m[0];
+        M[o.j * d + o.k] = r.m[1];
+        M[o.k * d + o.j] = r.m[2];
+        M[o.k * d + o.k] = r.m[3];
+        break;
+    case OP_DIAG:
+        for (int l = 0; l < d; ++l) M[l * d + l] = ((o.mask >> l) & 1) ? r.m[l] : cd(1, 0);
+        break;
+    case OP_SHIFT:
+        for (int x = 0; x < d; ++x) M[((x + o.s) % d) * d + x] = 1;
+        break;
+    }
+    return M;
+}
+
+// --------------------------------------------------------------- planning
+int default_tile_qudits(int d, bool c128) {
+    // largest nt with d^nt amplitudes <= 8192 (complex64) / 4096 (complex128)
+    const long long cap = c128 ? 4096 : 8192;
+    int nt = 0;
+    long long t = 1;
+    while (t * d <= cap) {
+        t *= d;
+        ++nt;
+    }
+    return nt;
+}
+
+int min_low_qudits(int d) {
+    int r = 0;
+    long long t = 1;
+    while (t < 32) {
+        t *= d;
+        ++r;
+    }
+    return r;
+}
+
+TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL) {
+    TileGeom g;
+    std::memset(&g, 0, sizeof(g));
+    g.kA = (int)active.size();
+    g.rL = rL;
+    g.nt = g.kA + rL;
+    g.T = (int)ipow_ll(d, g.nt);
+    g.SEG = (int)ipow_ll(d, rL);
+    g.ntiles = ipow_ll(d, n) / g.T;
+    for (int i = 0; i < g.kA; ++i) g.strideA[i] = ipow_ll(d, n - 1 - active[i]);
+    // outer runs from the least significant qudit (n - rL - 1) upwards
+    std::vector<bool> is_act(n, false);
+    for (int q : active) is_act[q] = true;
+    int nr = 0;
+    int q = n - rL - 1;
+    while (q >= 0) {
+        if (is_act[q]) { --q; continue; }
+        int hi = q;
+        while (q >= 0 && !is_act[q]) --q;
+        int len = hi - q;  // qudits q+1 .. hi
+        g.runM[nr] = ipow_ll(d, len);
+        g.runS[nr] = ipow_ll(d, n - 1 - hi);
+        ++nr;
+    }
+    g.nruns = nr;
+    g.divSEG = FastDiv((uint32_t)g.SEG);
+    return g;
+}
+
+int local_pos(const TileGeom &g, const std::vector<int> &active, int n, int q) {
+    if (q >= n - g.rL) return g.kA + (q - (n - g.rL));
+    for (int i = 0; i < (int)active.size(); ++i)
+        if (active[i] == q) return i;
+    return -1;
+}
+
+TOp localize(const TOp &op, const TileGeom &g, const std::vector<int> &active, int n, int d) {
+    TOp o = op;
+    auto lstride = [&](int p) { return (int)ipow_ll(d, g.nt - 1 - p); };
+    o.a = local_pos(g, active, n, op.a);
+    o.lsa = lstride(o.a);
+    o.fa = FastDiv((uint32_t)o.lsa);
+    if (is_controlled(op) || op.kind == OP_SWAP) {
+        o.c = local_pos(g, active, n, op.c);
+        o.lsc = lstride(o.c);
+        o.fc = FastDiv((uint32_t)o.lsc);
+    }
+    if (op.kind == OP_DENSEK)
+        for (int i = 0; i < op.nq; ++i) o.q[i] = local_pos(g, active, n, op.q[i]);
+    return o;
+}
+
+static void gate_qudits(const HGate &g, std::vector<int> &out) {
+    out.clear();
+    for (int i = 0; i < g.nq; ++i) out.push_back(g.q[i]);
+}
+
+static bool single_qudit_gate(const HGate &g) {
+    return g.nq == 1 && (g.kind == G_H || g.kind == G_X || g.kind == G_Z || g.kind == G_ROT || g.kind == G_DENSE);
+}
+
+// Which rL (largest) lets the qudit set fit nt_max local qudits; -1 if none.
+static int fit_rl(const std::vector<bool> &inset, int n, int nt_max, int rl_min) {
+    int top = std::min(nt_max, n);
+    for (int rL = top; rL >= std::min(rl_min, top); --rL) {
+        int kA = 0;
+        for (int q = 0; q < n - rL; ++q) kA += inset[q] ? 1 : 0;
+        if (kA + rL <= nt_max && kA <= kMaxActive) return rL;
+    }
+    return -1;
+}
+
+std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse) {
+    std::vector<PassPlan> plan;
+    const int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
+    const int rl_min = std::min(min_low_qudits(d), nt_max);
+    std::vector<int> remaining(gates.size());
+    for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
+    std::vector<int> qs;
+
+    auto finish = [&](std::vector<int> &members, std::vector<bool> &inset) {
+        PassPlan p;
+        int rL = fit_rl(inset, n, nt_max, rl_min);
+        if (rL < 0) rL = fit_rl(inset, n, nt_max, 0);   // a lone wide gate may need SEG < 32
+        std::vector<int> active;
+        for (int q = 0; q < n - rL; ++q)
+            if (inset[q]) active.push_back(q);
+        // group consecutive single-qudit gates on the same qudit
+        std::vector<int> last_op_on(n, -1);  // op index touching qudit last
+        for (int gi : members) {
+            const HGate &g = gates[gi];
+            if (fuse && single_qudit_gate(g) && last_op_on[g.q[0]] >= 0) {
+                std::vector<int> &grp = p.groups[last_op_on[g.q[0]]];
+                const HGate &g0 = gates[grp[0]];
+                if (single_qudit_gate(g0)) {
+                    grp.push_back(gi);
+                    continue;
+                }
+            }
+            p.groups.push_back({gi});
+            for (int i = 0; i < g.nq; ++i) last_op_on[g.q[i]] = (int)p.groups.size() - 1;
+        }
+        // a lone gate on one wide target goes through the strided kernel
+        if (p.groups.size() == 1 && p.groups[0].size() == 1) {
+            const HGate &g = gates[p.groups[0][0]];
+            int target = (g.kind == G_CROT || g.kind == G_SUM) ? g.q[1] : g.q[0];
+            bool strided_ok = (single_qudit_gate(g) && !(g.kind == G_DENSE && g.nq != 1)) || g.kind == G_CROT ||
+                              g.kind == G_SUM;
+            if (strided_ok && ipow_ll(d, n - 1 - target) >= kWideMin && ipow_ll(d, n - 1 - target) < (1ll << 31)) {
+                p.strided = true;
+                plan.push_back(p);
+                return;
+            }
+        }
+        p.active = active;
+        p.geom = make_geom(d, n, active, rL);
+        plan.push_back(p);
+    };
+
+    while (!remaining.empty()) {
+        std::vector<bool> inset(n, false), blocked(n, false);
+        std::vector<int> members, deferred;
+        size_t scan = 0;
+        for (; scan < remaining.size(); ++scan) {
+            const int gi = remaining[scan];
+            gate_qudits(gates[gi], qs);
+            bool is_blocked = false;
+            for (int q : qs) is_blocked |= blocked[q];
+            bool take = false;
+            if (!is_blocked && (int)members.size() < kMaxTileOps && (fuse || members.empty())) {
+                std::vector<bool> trial = inset;
+                for (int q : qs) trial[q] = true;
+                if (fit_rl(trial, n, nt_max, rl_min) >= 0) {
+                    inset = trial;
+                    take = true;
+                }
+            }
+            if (take) {
+                members.push_back(gi);
+            } else {
+                deferred.push_back(gi);
+                for (int q : qs) blocked[q] = true;
+                if (!fuse) { ++scan; break; }
+                // stop scanning once every qudit is blocked
+                bool all = true;
+                for (int q = 0; q < n && all; ++q) all = blocked[q];
+                if (all) { ++scan; break; }
+            }
+        }
+        for (; scan < remaining.size(); ++scan) deferred.push_back(remaining[scan]);
+        if (members.empty()) {
+            // cannot happen for valid gates (any gate fits an empty tile)
+            members.push_back(deferred.front());
+            deferred.erase(deferred.begin());
+            gate_qudits(gates[members[0]], qs);
+            for (int q : qs) inset[q] = true;
+        }
+        finish(members, inset);
+        remaining.swap(deferred);
+    }
+    return plan;
+}
+
+}  // namespace qf

@@ -1,0 +1,119 @@
+// qf_host.h -- host-side internals of libqf: recorded gates, gate entries,
+// pass planning and the launchers the kernels export.
+#pragma once
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "qf_internal.cuh"
+
+namespace qf {
+
+using cd = std::complex<double>;
+
+// ---- kernel launchers (defined next to their kernels)
+template <typename R>
+cudaError_t launch_strided(const Launch &L, cplx<R> *psi, int d, int n, const TOp &op, const cplx<R> *mat, int nmat);
+template <typename R>
+cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g, int nops, const TOp *ops_dev,
+                        const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i);
+template <typename R>
+size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat);
+template <typename R>
+cudaError_t launch_basis(const Launch &L, cplx<R> *psi, long long N, long long index);
+template <typename R>
+cudaError_t launch_expect_number(const Launch &L, const cplx<R> *psi, int d, int n, double *partials, double *out_dev);
+template <typename R>
+cudaError_t launch_fibre_reduce(const Launch &L, const cplx<R> *psi, int d, int n, int q, int kind, const double2 *obs_dev,
+                                double *partials, double *out_dev);
+int reduce_max_blocks(int num_sms);
+
+// ---- errors
+qf_status set_error(qf_status s, const std::string &msg);
+qf_status cuda_error(cudaError_t e, const char *where);
+
+// ---- recorded gates (program entries and immediate calls share this form)
+enum GateKind { G_DENSE = 0, G_ROT, G_CROT, G_SUM, G_SWAP, G_X, G_Z, G_H };
+
+struct HGate {
+    int kind = G_DENSE;
+    int nq = 0;
+    int q[6] = {0, 0, 0, 0, 0, 0};   // targets; crot/sum: (c, t); swap: (a, b)
+    int j = 0, k = 0;
+    char axis = 'x';
+    int slot = -1;                   // parameter slot, -1 = fixed theta
+    double theta = 0.0;
+    int power = 0;                   // X shift / Z power
+    std::vector<cd> U;               // G_DENSE: d^nq x d^nq row-major
+};
+
+// Validates a gate against (d, n); returns QF_OK or QF_ERR_ARG with message.
+qf_status check_gate(const HGate &g, int d, int n);
+
+// A resolved op: kind (OpKind) on global qudits plus FP64 entries.
+struct ROp {
+    TOp op;                 // a/c/q[] are GLOBAL qudit indices here
+    std::vector<cd> m;      // matrix entries in the layout of op.kind
+};
+
+// Entries of a gate at angle theta (theta ignored for fixed gates).
+ROp resolve_gate(const HGate &g, int d, double theta);
+// theta of a gate given the parameter vector.
+double gate_angle(const HGate &g, const double *params);
+// Generator-scaled derivative support: returns false if the gate has no angle.
+bool gate_is_param(const HGate &g);
+
+// True if the op only moves the qudit it targets (a d x d action).
+inline bool is_single(const TOp &o) {
+    return o.kind == OP_DENSE || o.kind == OP_PAIR || o.kind == OP_DIAG || o.kind == OP_SHIFT;
+}
+inline bool is_controlled(const TOp &o) { return o.kind == OP_CPAIR || o.kind == OP_CDIAG || o.kind == OP_CSHIFT; }
+
+// d x d matrix of a single-qudit resolved op.
+std::vector<cd> dense_of(const ROp &r, int d);
+
+// ---- planning
+struct PassPlan {
+    bool strided = false;               // one op through the strided kernel
+    TileGeom geom;                      // tile passes
+    std::vector<std::vector<int>> groups;  // per op of the pass: gate indices merged (in order)
+    std::vector<int> active;            // active qudits (sorted)
+};
+
+int default_tile_qudits(int d, bool c128);   // nt_max
+int min_low_qudits(int d);                   // rL_min (SEG >= 32)
+long long ipow_ll(int d, int e);
+
+// Plans passes over `gates` (indices into the gate list).  fuse = false gives
+// one pass per gate.
+std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse);
+
+// Tile geometry for the given active qudits and low-qudit count.
+TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);
+// Local position of global qudit q in a tile geometry (-1 if not in the tile).
+int local_pos(const TileGeom &g, const std::vector<int> &active, int n, int q);
+// Converts a resolved op on global qudits into tile-local form.
+TOp localize(const TOp &op, const TileGeom &g, const std::vector<int> &active, int n, int d);
+
+}  // namespace qf
+
+// The opaque handle of include/qf.h.
+struct qf_state {
+    int d = 0, n = 0;
+    qf_dtype dt = QF_C64;
+    long long N = 0;
+    void *data = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    double *d_partials = nullptr;    // reduction scratch
+    double *d_out = nullptr;         // reduction results
+    double *h_out = nullptr;         // pinned copy of results
+    // uploads of large matrices (custom gates, observables)
+    void *h_up = nullptr;
+    void *d_up = nullptr;
+    size_t up_cap = 0;
+    cudaEvent_t up_ev = nullptr;
+    bool up_pending = false;
+};

@@ -1,0 +1,420 @@
+"""Thin Python binding of libqf (include/qf.h).
+
+Every ``qf_*`` function here marshals its arguments and calls the C entry
+point of the same name; every step of the simulation runs in the library's
+CUDA kernels.  PyTorch is used only to own device memory and to supply the
+current CUDA stream.  Errors raise ``QFError`` with the library's message.
+There is no CPU fallback: if libqf.so has not been built the import of the
+library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+QF_OK, QF_ERR_ARG, QF_ERR_OOM, QF_ERR_CUDA, QF_ERR_TIMEOUT, QF_ERR_UNSUPPORTED = range(6)
+QF_C64, QF_C128 = 0, 1
+QF_OBS_NUMBER_ALL, QF_OBS_NORM, QF_OBS_HERMITIAN, QF_OBS_MARGINAL = range(4)
+STATUS_NAMES = {0: "QF_OK", 1: "QF_ERR_ARG", 2: "QF_ERR_OOM", 3: "QF_ERR_CUDA", 4: "QF_ERR_TIMEOUT",
+                5: "QF_ERR_UNSUPPORTED"}
+
+
+class QFError(RuntimeError):
+    def __init__(self, func: str, status: int, message: str):
+        super().__init__("%s failed: %s: %s" % (func, STATUS_NAMES.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+class qf_obs(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("q", ctypes.c_int), ("matrix", ctypes.POINTER(ctypes.c_double))]
+
+
+_c = ctypes
+_vp = _c.c_void_p
+_int = _c.c_int
+_dbl = _c.c_double
+_PROTOS = {
+    "qf_last_error": (_c.c_char_p, []),
+    "qf_expect_size": (_int, [_int, _int, _c.POINTER(qf_obs)]),
+    "qf_state_init": (_int, [_int, _int, _int, _vp, _c.POINTER(_vp)]),
+    "qf_state_wrap": (_int, [_int, _int, _int, _vp, _vp, _c.POINTER(_vp)]),
+    "qf_state_free": (_int, [_vp]),
+    "qf_state_ptr": (_int, [_vp, _c.POINTER(_vp), _c.POINTER(_c.c_longlong)]),
+    "qf_state_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
+    "qf_state_set_stream": (_int, [_vp, _vp]),
+    "qf_state_set_basis": (_int, [_vp, _c.c_longlong]),
+    "qf_state_copy": (_int, [_vp, _vp]),
+    "qf_apply_gate": (_int, [_vp, _c.POINTER(_int), _int, _c.POINTER(_dbl)]),
+    "qf_apply_rot": (_int, [_vp, _int, _int, _int, _dbl, _c.c_char]),
+    "qf_apply_crot": (_int, [_vp, _int, _int, _int, _int, _dbl, _c.c_char]),
+    "qf_apply_sum": (_int, [_vp, _int, _int]),
+    "qf_apply_swap": (_int, [_vp, _int, _int]),
+    "qf_apply_x": (_int, [_vp, _int, _int]),
+    "qf_apply_z": (_int, [_vp, _int, _int]),
+    "qf_apply_h": (_int, [_vp, _int]),
+    "qf_expect": (_int, [_vp, _c.POINTER(qf_obs), _c.POINTER(_dbl)]),
+    "qf_expect_device": (_int, [_vp, _c.POINTER(qf_obs), _vp]),
+    "qf_program_create": (_int, [_int, _int, _c.POINTER(_vp)]),
+    "qf_program_free": (_int, [_vp]),
+    "qf_program_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int)]),
+    "qf_program_add_gate": (_int, [_vp, _c.POINTER(_int), _int, _c.POINTER(_dbl)]),
+    "qf_program_add_rot": (_int, [_vp, _int, _int, _int, _c.c_char, _int, _dbl]),
+    "qf_program_add_crot": (_int, [_vp, _int, _int, _int, _int, _c.c_char, _int, _dbl]),
+    "qf_program_add_sum": (_int, [_vp, _int, _int]),
+    "qf_program_add_swap": (_int, [_vp, _int, _int]),
+    "qf_program_add_x": (_int, [_vp, _int, _int]),
+    "qf_program_add_z": (_int, [_vp, _int, _int]),
+    "qf_program_add_h": (_int, [_vp, _int]),
+    "qf_program_set_fusion": (_int, [_vp, _int]),
+    "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
+    "qf_program_last_passes": (_int, [_vp]),
+    "qf_program_plan": (_int, [_vp, _int, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
+    "qf_program_set_timing": (_int, [_vp, _int]),
+    "qf_program_pass_times": (_int, [_vp, _int, _c.POINTER(_c.c_float), _c.POINTER(_int), _c.POINTER(_dbl),
+                                     _c.POINTER(_int)]),
+}
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libqf.so; raises ImportError if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libqf.so not built at %s: run __graft_entry__.build() first" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _call(name: str, *args) -> None:
+    st = getattr(lib(), name)(*args)
+    if st != QF_OK:
+        raise QFError(name, st, lib().qf_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_c.POINTER(_dbl))
+
+
+def _cmatrix(U) -> np.ndarray:
+    """Row-major interleaved FP64 copy of a complex matrix."""
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.complex128))
+    return np.ascontiguousarray(U.view(np.float64).reshape(-1))
+
+
+# ------------------------------------------------------------------ states
+def qf_last_error() -> str:
+    return lib().qf_last_error().decode()
+
+
+def qf_state_init(d: int, n: int, dtype: int = QF_C64, stream=None) -> int:
+    h = _vp()
+    _call("qf_state_init", d, n, dtype, _stream_ptr(stream), _c.byref(h))
+    return h.value
+
+
+def qf_state_wrap(d: int, n: int, dtype: int, dev_ptr: int, stream=None) -> int:
+    h = _vp()
+    _call("qf_state_wrap", d, n, dtype, dev_ptr, _stream_ptr(stream), _c.byref(h))
+    return h.value
+
+
+def qf_state_free(s: int) -> None:
+    _call("qf_state_free", s)
+
+
+def qf_state_ptr(s: int):
+    p, n = _vp(), _c.c_longlong()
+    _call("qf_state_ptr", s, _c.byref(p), _c.byref(n))
+    return p.value, n.value
+
+
+def qf_state_info(s: int):
+    """(d, n, dtype) of a state."""
+    d, n, dt = _int(), _int(), _int()
+    _call("qf_state_info", s, _c.byref(d), _c.byref(n), _c.byref(dt))
+    return d.value, n.value, dt.value
+
+
+def qf_state_set_stream(s: int, stream=None) -> None:
+    _call("qf_state_set_stream", s, _stream_ptr(stream))
+
+
+def qf_state_set_basis(s: int, index: int) -> None:
+    _call("qf_state_set_basis", s, int(index))
+
+
+def qf_state_copy(dst: int, src: int) -> None:
+    _call("qf_state_copy", dst, src)
+
+
+# ------------------------------------------------------------------ gates
+def qf_apply_gate(s: int, targets: Sequence[int], U) -> None:
+    t = (_int * len(targets))(*[int(x) for x in targets])
+    m = _cmatrix(U)
+    _call("qf_apply_gate", s, t, len(targets), _dptr(m))
+
+
+def qf_apply_rot(s: int, q: int, j: int, k: int, theta: float, axis: str) -> None:
+    _call("qf_apply_rot", s, q, j, k, float(theta), axis.encode())
+
+
+def qf_apply_crot(s: int, c: int, t: int, j: int, k: int, theta: float, axis: str) -> None:
+    _call("qf_apply_crot", s, c, t, j, k, float(theta), axis.encode())
+
+
+def qf_apply_sum(s: int, c: int, t: int) -> None:
+    _call("qf_apply_sum", s, c, t)
+
+
+def qf_apply_swap(s: int, a: int, b: int) -> None:
+    _call("qf_apply_swap", s, a, b)
+
+
+def qf_apply_x(s: int, q: int, shift: int = 1) -> None:
+    _call("qf_apply_x", s, q, int(shift))
+
+
+def qf_apply_z(s: int, q: int, power: int = 1) -> None:
+    _call("qf_apply_z", s, q, int(power))
+
+
+def qf_apply_h(s: int, q: int) -> None:
+    _call("qf_apply_h", s, q)
+
+
+# ------------------------------------------------------------------ measurement
+def _obs(kind: int, q: int = 0, matrix=None):
+    o = qf_obs()
+    o.kind, o.q = kind, q
+    keep = None
+    if matrix is not None:
+        keep = _cmatrix(matrix)
+        o.matrix = _dptr(keep)
+    return o, keep
+
+
+def qf_expect_size(d: int, n: int, kind: int) -> int:
+    o, _ = _obs(kind)
+    return lib().qf_expect_size(d, n, _c.byref(o))
+
+
+def qf_expect(s: int, kind: int = QF_OBS_NUMBER_ALL, q: int = 0, matrix=None) -> np.ndarray:
+    """Host FP64 results (synchronises the state's stream)."""
+    o, keep = _obs(kind, q, matrix)
+    d, n, _ = qf_state_info(s)
+    out = np.zeros(max(1, lib().qf_expect_size(d, n, _c.byref(o))))
+    _call("qf_expect", s, _c.byref(o), _dptr(out))
+    del keep
+    return out
+
+
+def qf_expect_device(s: int, out_dev_ptr: int, kind: int = QF_OBS_NUMBER_ALL, q: int = 0, matrix=None) -> None:
+    o, keep = _obs(kind, q, matrix)
+    _call("qf_expect_device", s, _c.byref(o), out_dev_ptr)
+    del keep
+
+
+# ------------------------------------------------------------------ programs
+def qf_program_create(d: int, n: int) -> int:
+    h = _vp()
+    _call("qf_program_create", d, n, _c.byref(h))
+    return h.value
+
+
+def qf_program_free(p: int) -> None:
+    _call("qf_program_free", p)
+
+
+def qf_program_info(p: int):
+    g, k = _int(), _int()
+    _call("qf_program_info", p, _c.byref(g), _c.byref(k))
+    return g.value, k.value
+
+
+def qf_program_add_gate(p: int, targets: Sequence[int], U) -> None:
+    t = (_int * len(targets))(*[int(x) for x in targets])
+    m = _cmatrix(U)
+    _call("qf_program_add_gate", p, t, len(targets), _dptr(m))
+
+
+def qf_program_add_rot(p: int, q: int, j: int, k: int, axis: str, param_slot: int = -1, theta: float = 0.0) -> None:
+    _call("qf_program_add_rot", p, q, j, k, axis.encode(), int(param_slot), float(theta))
+
+
+def qf_program_add_crot(p: int, c: int, t: int, j: int, k: int, axis: str, param_slot: int = -1,
+                        theta: float = 0.0) -> None:
+    _call("qf_program_add_crot", p, c, t, j, k, axis.encode(), int(param_slot), float(theta))
+
+
+def qf_program_add_sum(p: int, c: int, t: int) -> None:
+    _call("qf_program_add_sum", p, c, t)
+
+
+def qf_program_add_swap(p: int, a: int, b: int) -> None:
+    _call("qf_program_add_swap", p, a, b)
+
+
+def qf_program_add_x(p: int, q: int, shift: int = 1) -> None:
+    _call("qf_program_add_x", p, q, int(shift))
+
+
+def qf_program_add_z(p: int, q: int, power: int = 1) -> None:
+    _call("qf_program_add_z", p, q, int(power))
+
+
+def qf_program_add_h(p: int, q: int) -> None:
+    _call("qf_program_add_h", p, q)
+
+
+def qf_program_set_fusion(p: int, enable: bool) -> None:
+    _call("qf_program_set_fusion", p, 1 if enable else 0)
+
+
+def qf_program_run(p: int, s: int, params=None) -> None:
+    if params is None:
+        _call("qf_program_run", p, s, None)
+    else:
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        _call("qf_program_run", p, s, _dptr(a))
+
+
+def qf_program_last_passes(p: int) -> int:
+    return lib().qf_program_last_passes(p)
+
+
+def qf_program_set_timing(p: int, enable: bool) -> None:
+    _call("qf_program_set_timing", p, 1 if enable else 0)
+
+
+def qf_program_pass_times(p: int, max_passes: int = 4096):
+    """(ms, kind, bytes) arrays for the passes of the last timed run."""
+    ms = np.zeros(max_passes, dtype=np.float32)
+    kind = np.zeros(max_passes, dtype=np.int32)
+    by = np.zeros(max_passes)
+    cnt = _int()
+    _call("qf_program_pass_times", p, max_passes, ms.ctypes.data_as(_c.POINTER(_c.c_float)),
+          kind.ctypes.data_as(_c.POINTER(_int)), _dptr(by), _c.byref(cnt))
+    k = min(cnt.value, max_passes)
+    return ms[:k].astype(np.float64), kind[:k], by[:k]
+
+
+def qf_program_plan(p: int, dtype: int = QF_C64):
+    """(passes, strided passes, max ops per pass) of the program's plan."""
+    a, b, c = _int(), _int(), _int()
+    _call("qf_program_plan", p, dtype, _c.byref(a), _c.byref(b), _c.byref(c))
+    return a.value, b.value, c.value
+
+
+# ------------------------------------------------------------------ helpers
+class State:
+    """A state whose amplitudes live in a torch tensor (complex64 or
+    complex128) on the current CUDA device, wrapped by a libqf handle."""
+
+    def __init__(self, d: int, n: int, dtype: str = "c64", stream=None, tensor=None):
+        import torch
+        self.d, self.n = d, n
+        self.dtype = QF_C64 if dtype in ("c64", "complex64") else QF_C128
+        tdt = torch.complex64 if self.dtype == QF_C64 else torch.complex128
+        N = d ** n
+        if tensor is None:
+            tensor = torch.empty(N, dtype=tdt, device="cuda")
+        assert tensor.dtype == tdt and tensor.is_cuda and tensor.numel() == N and tensor.is_contiguous()
+        self.tensor = tensor
+        self.handle = qf_state_wrap(d, n, self.dtype, tensor.data_ptr(), stream)
+
+    def set_basis(self, index: int = 0) -> "State":
+        qf_state_set_basis(self.handle, index)
+        return self
+
+    def expect_number(self) -> np.ndarray:
+        """<N_q> for every qudit, then the norm (n + 1 FP64 values)."""
+        return qf_expect(self.handle, QF_OBS_NUMBER_ALL)
+
+    def free(self) -> None:
+        if self.handle:
+            qf_state_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def apply_ops(s: int, ops: Iterable, params=None) -> None:
+    """Applies workload ops one by one through the immediate entry points."""
+    for op in ops:
+        k = op.kind
+        if k == "h":
+            qf_apply_h(s, op.qudits[0])
+        elif k == "x":
+            qf_apply_x(s, op.qudits[0], op.power)
+        elif k == "z":
+            qf_apply_z(s, op.qudits[0], op.power)
+        elif k == "rot":
+            qf_apply_rot(s, op.qudits[0], op.j, op.k, op.angle(params), op.axis)
+        elif k == "crot":
+            qf_apply_crot(s, op.qudits[0], op.qudits[1], op.j, op.k, op.angle(params), op.axis)
+        elif k == "sum":
+            qf_apply_sum(s, op.qudits[0], op.qudits[1])
+        elif k == "swap":
+            qf_apply_swap(s, op.qudits[0], op.qudits[1])
+        elif k == "u":
+            qf_apply_gate(s, op.qudits, op.matrix)
+        else:
+            raise ValueError(k)
+
+
+def program_from_ops(d: int, n: int, ops: Iterable, fuse: bool = True) -> int:
+    """Records workload ops into a new program (parameter slots kept)."""
+    p = qf_program_create(d, n)
+    for op in ops:
+        k = op.kind
+        if k == "h":
+            qf_program_add_h(p, op.qudits[0])
+        elif k == "x":
+            qf_program_add_x(p, op.qudits[0], op.power)
+        elif k == "z":
+            qf_program_add_z(p, op.qudits[0], op.power)
+        elif k == "rot":
+            qf_program_add_rot(p, op.qudits[0], op.j, op.k, op.axis, op.param, op.theta)
+        elif k == "crot":
+            qf_program_add_crot(p, op.qudits[0], op.qudits[1], op.j, op.k, op.axis, op.param, op.theta)
+        elif k == "sum":
+            qf_program_add_sum(p, op.qudits[0], op.qudits[1])
+        elif k == "swap":
+            qf_program_add_swap(p, op.qudits[0], op.qudits[1])
+        elif k == "u":
+            qf_program_add_gate(p, op.qudits, op.matrix)
+        else:
+            raise ValueError(k)
+    qf_program_set_fusion(p, fuse)
+    return p
