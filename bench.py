@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Gate-application throughput of random qudit circuits on GB300.
+
+Workload (one step): a seeded random sequence of 200 gates -- each drawn
+uniformly from {Haar-random d x d unitary, level-pair rotation with uniform
+angle, clock Z, shift X, SUM or controlled-RY on a random ordered pair} -- is
+applied to each of four complex64 states, d=2 n=28, d=3 n=17, d=4 n=14 and
+d=5 n=12 (1.29e8 to 2.68e8 amplitudes, 1.0 to 2.1 GB each, every state far
+larger than L2), through fused programs, followed by <N_q> of every qudit in
+FP64.  Throughput is amplitude-updates/s: N x gates applied / time.
+
+Reported alongside: HBM roofline of the fused tile kernel (bytes-weighted over
+its launches in the timed region, CUDA events around every pass), the per-gate
+strided-kernel GB/s sweep over gate kinds and target positions on d=3 n=17,
+complex128 and unfused throughput, end-to-end throughput through the public
+API with host buffers, SM clocks sampled during the timed region, and the
+CPU oracle timed on the host cores on a bounded sample.
+
+--impl reference times the CPU oracle (complex128, explicit loops, OpenMP over
+independent amplitude groups) on the host cores on the same workload, each step
+a bounded sample (one gate per state), and prints the same JSON line with
+"impl": "reference".
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SIZES = [(2, 28), (3, 17), (4, 14), (5, 12)]
+N_GATES = 200
+METRIC = "amplitude-updates/s (random 200-gate qudit circuits, fused)"
+UNIT = "amplitude-updates/s"
+WORKLOAD = "random-200-gate sequences on d=2 n=28, d=3 n=17, d=4 n=14, d=5 n=12 + <N_q> of every qudit"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip c128/unfused/sweep/e2e/cpu legs")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small run for ncu captures: d=3 n=17 complex64 only, no extras")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, n = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": n}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_tile.cu", "qf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2409_17716_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratio():
+    """DRAM bytes / algorithmic bytes of one tile-kernel launch from the
+    committed ncu summary, or None if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        if j.get("kernel_sha") != kernel_hash():
+            return None
+        return float(j["dram_bytes_per_launch"]) / float(j["algorithmic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import sim
+    from paper_2409_17716_gb300 import workloads as W
+
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    sizes = SIZES if not args.profile_case else [(3, 17)]
+    states, circuits, pos = [], [], []
+    for d, n in sizes:
+        states.append(sim.basis(d, n, 0))
+        circuits.append(W.random_circuit(d, n, N_GATES))
+        pos.append(0)
+
+    def step():
+        au = 0
+        for i, (d, n) in enumerate(sizes):
+            op = circuits[i][pos[i] % N_GATES]
+            pos[i] += 1
+            t, U = sim.op_matrix(op, d)
+            sim.apply(states[i], d, n, t, U)
+            au += d ** n
+        return au
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    au = 0
+    for _ in range(args.steps):
+        au += step()
+    dt = time.perf_counter() - t0
+    value = au / dt
+    sample = "one gate per state per step (the next gate of each 200-gate sequence), complex128 oracle"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "global_batch": len(sizes), "seq_len": None,
+                       "parallelism": "cpu-oracle", "l2": "states larger than L2"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- CPU baseline leg
+def cpu_baseline(budget_s=20.0):
+    """The oracle as it stands on the host cores: gates of the d=3 n=17
+    sequence on a complex128 state until ~budget_s of work."""
+    import numpy as np
+    from oracle import sim
+    from paper_2409_17716_gb300 import workloads as W
+    d, n = 3, 17
+    cores = os.cpu_count() or 1
+    psi = sim.basis(d, n, 0)
+    ops = W.random_circuit(d, n, N_GATES)
+    t0 = time.perf_counter()
+    g = 0
+    while g < N_GATES and (time.perf_counter() - t0) < budget_s:
+        t, U = sim.op_matrix(ops[g], d)
+        sim.apply(psi, d, n, t, U)
+        g += 1
+    dt = time.perf_counter() - t0
+    return {"value": g * d ** n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d gates of the d=3 n=17 sequence, complex128 oracle, %.1f s" % (g, dt)}
+
+
+# --------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2409_17716_gb300 import build as gpu_build
+    gpu_build.build()
+    from paper_2409_17716_gb300 import qf
+    from paper_2409_17716_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    hbm_peak, peak_kind = peaks()
+    sizes = [(3, 17)] if args.profile_case else SIZES
+    extras = not (args.no_extras or args.profile_case)
+    stream = torch.cuda.current_stream()
+
+    # ---- states and fused programs (inputs resident in HBM)
+    states, progs, circ = [], [], []
+    for d, n in sizes:
+        st = qf.State(d, n, "c64")
+        st.set_basis(0)
+        ops = W.random_circuit(d, n, N_GATES)
+        p = qf.program_from_ops(d, n, ops, fuse=True)
+        states.append(st)
+        progs.append(p)
+        circ.append(ops)
+    out_dev = torch.zeros(128, dtype=torch.float64, device="cuda")
+
+    def step(states_, progs_):
+        for st, p in zip(states_, progs_):
+            qf.qf_program_run(p, st.handle)
+            qf.qf_expect_device(st.handle, out_dev.data_ptr(), qf.QF_OBS_NUMBER_ALL)
+
+    for _ in range(args.warmup):
+        step(states, progs)
+    torch.cuda.synchronize()
+    passes = [qf.qf_program_last_passes(p) for p in progs]
+    for p in progs:
+        qf.qf_program_set_timing(p, True)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(states, progs)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+
+    # per-pass times of every timed step
+    tile_ms, tile_bytes, strided_ms, strided_bytes, n_tile = 0.0, 0.0, 0.0, 0.0, 0
+    for p in progs:
+        pms, pkind, pby = qf.qf_program_pass_times(p, 1 << 16)
+        qf.qf_program_set_timing(p, False)
+        for t_, k_, b_ in zip(pms, pkind, pby):
+            if k_ == 0:
+                tile_ms += t_
+                tile_bytes += b_
+                n_tile += 1
+            else:
+                strided_ms += t_
+                strided_bytes += b_
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    au_step = sum(d ** n for d, n in sizes) * N_GATES
+    value = au_step * args.steps * world / (ms / 1e3)
+    launches = sum(pp + 2 for pp in passes) * args.steps
+    achieved = (tile_bytes / (tile_ms / 1e3)) / 1e9 if tile_ms > 0 else None
+    ratio = traffic_ratio()
+    avg_alg = tile_bytes / n_tile if n_tile else None
+    roofline = {"bound": "hbm", "kernel": "k_tile (fused pass)", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
+                "traffic": (ratio * avg_alg) if (ratio and avg_alg) else None,
+                "algorithmic_bytes_per_launch": avg_alg, "launches": n_tile,
+                "share_of_step": tile_ms / ms if ms else None,
+                "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy)" if peak_kind == "measured" else peak_kind}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if not args.profile_case else "profile case: d=3 n=17 only",
+                       "global_batch": len(sizes) * world, "seq_len": None,
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "l2": "inputs larger than L2 (1.0-2.1 GB per state), no flush",
+                       "passes_per_step": passes, "gates_per_state": N_GATES},
+            "gpu_launches": launches, "clocks": clocks, "roofline": roofline}
+
+    if extras:
+        line["per_size"] = per_size_throughput(qf, W, torch, sizes, states, progs, args)
+        line["unfused"] = unfused_throughput(qf, W, torch, sizes, states, circ)
+        line["c128"] = c128_throughput(qf, W, torch, sizes)
+        line["per_gate"] = per_gate_sweep(qf, W, torch, hbm_peak)
+        line["e2e"] = e2e_throughput(qf, W, torch, sizes, progs, args)
+    for p in progs:
+        qf.qf_program_free(p)
+    for st in states:
+        st.free()
+    if extras and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_ms(torch, fn, reps=3):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def per_size_throughput(qf, W, torch, sizes, states, progs, args):
+    out = []
+    for (d, n), st, p in zip(sizes, states, progs):
+        ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=5)
+        out.append({"d": d, "n": n, "amps": d ** n, "passes": qf.qf_program_last_passes(p),
+                    "ms": ms, "au_per_s": d ** n * N_GATES / (ms / 1e3)})
+    return out
+
+
+def unfused_throughput(qf, W, torch, sizes, states, circ):
+    tot_au, tot_ms = 0, 0.0
+    for (d, n), st, ops in zip(sizes, states, circ):
+        p = qf.program_from_ops(d, n, ops, fuse=False)
+        qf.qf_program_run(p, st.handle)
+        ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=2)
+        qf.qf_program_free(p)
+        tot_au += d ** n * N_GATES
+        tot_ms += ms
+    return {"value": tot_au / (tot_ms / 1e3), "unit": UNIT, "note": "one kernel per gate (fusion off)"}
+
+
+def c128_throughput(qf, W, torch, sizes):
+    tot_au, tot_ms, per = 0, 0.0, []
+    for d, n in sizes:
+        st = qf.State(d, n, "c128").set_basis(0)
+        p = qf.program_from_ops(d, n, W.random_circuit(d, n, N_GATES), fuse=True)
+        qf.qf_program_run(p, st.handle)
+        ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=3)
+        per.append({"d": d, "n": n, "ms": ms, "passes": qf.qf_program_last_passes(p)})
+        qf.qf_program_free(p)
+        st.free()
+        tot_au += d ** n * N_GATES
+        tot_ms += ms
+    return {"value": tot_au / (tot_ms / 1e3), "unit": UNIT, "per_size": per}
+
+
+def per_gate_sweep(qf, W, torch, hbm_peak):
+    """Single-gate GB/s of each gate kind at every target position, d=3 n=17,
+    complex64 (strided kernel for stride >= 32, tile kernel below)."""
+    import numpy as np
+    d, n = 3, 17
+    N = d ** n
+    b = 8
+    st = qf.State(d, n, "c64").set_basis(0)
+    rng = np.random.default_rng(7)
+    U = W.haar_unitary(d, rng)
+    kinds = {
+        "dense(H/Haar)": (lambda q: qf.qf_apply_gate(st.handle, [q], U), 2 * N * b),
+        "rot_pair(RY 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "y"), 2 * N * b * 2 / d),
+        "diag(clock Z)": (lambda q: qf.qf_apply_z(st.handle, q, 1), 2 * N * b * (d - 1) / d),
+        "rz_pair(RZ 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "z"), 2 * N * b * 2 / d),
+        "shift(X)": (lambda q: qf.qf_apply_x(st.handle, q, 1), 2 * N * b),
+        "sum(c=q-1,t=q)": (lambda q: qf.qf_apply_sum(st.handle, (q - 1) % n, q), 2 * N * b * (d - 1) / d),
+    }
+    out = {}
+    for name, (fn, by) in kinds.items():
+        rows = []
+        for q in range(n):
+            fn(q)
+            ms = _time_ms(torch, lambda: fn(q), reps=5)
+            rows.append(by / (ms / 1e3) / 1e9)
+        wide = [r for q, r in enumerate(rows) if d ** (n - 1 - q) >= 32]
+        out[name] = {"gbps_by_target": [round(r, 1) for r in rows], "median_gbps": statistics.median(rows),
+                     "median_frac": statistics.median(rows) / hbm_peak,
+                     "median_frac_wide": (statistics.median(wide) / hbm_peak) if wide else None}
+    st.free()
+    return out
+
+
+def e2e_throughput(qf, W, torch, sizes, progs, args):
+    """Through the public API with host buffers: per step and state, copy the
+    input state from pinned host memory, run the program, read <N_q> back to
+    the host (qf_expect synchronises)."""
+    host = []
+    for d, n in sizes:
+        h = torch.zeros(d ** n, dtype=torch.complex64, pin_memory=True)
+        h[0] = 1.0
+        host.append(h)
+    states = [qf.State(d, n, "c64") for d, n in sizes]
+
+    def step():
+        for st, h, p in zip(states, host, progs):
+            st.tensor.copy_(h, non_blocking=True)
+            qf.qf_program_run(p, st.handle)
+            qf.qf_expect(st.handle, qf.QF_OBS_NUMBER_ALL)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for st in states:
+        st.free()
+    au = sum(d ** n for d, n in sizes) * N_GATES * steps
+    return {"value": au / dt, "unit": UNIT, "h2d_bytes_per_step": sum(d ** n * 8 for d, n in sizes),
+            "d2h_bytes_per_step": sum((n + 1) * 8 for d, n in sizes), "steps": steps}
+
+
+if __name__ == "__main__":
+    sys.exit(main())
