@@ -163,6 +163,28 @@ qf_status qf_expect(qf_state *s, const qf_obs *obs, double *out_host);
  * (8-byte aligned) asynchronously on the state's stream. */
 qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev);
 
+/* Allocation-free <N_q> (no counterpart in the paper; a deployment aid).
+ * For callers that cannot allocate device memory at the point of measurement
+ * -- code being recorded into a CUDA graph, host callbacks and latency-bound
+ * loops that must not trigger the device-wide synchronisation an allocation
+ * or free can cause, and hosts whose own memory pool holds the whole device
+ * heap.  Computes what qf_expect with QF_OBS_NUMBER_ALL computes:
+ * out_dev[q] = <N_q> for q < n and out_dev[n] = sum_i |psi_i|^2 (n + 1 FP64
+ * values, device memory, 8-byte aligned), from the caller's d^n amplitudes at
+ * psi_dev (device, 16-byte aligned, interleaved as dt), asynchronously on
+ * cuda_stream (a cudaStream_t, NULL = legacy default stream).  No qf_state is
+ * needed and nothing is allocated or freed: the per-CTA partial sums live in
+ * one fixed 256 KiB device array (512 rows of 64 doubles) that every device
+ * loading the library holds until the process exits.  Sizes: 2 <= d <= 16,
+ * 1 <= n with n + 1 <= 64; anything larger is rejected with QF_ERR_ARG and a
+ * message.  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture begins.  All calls share the array and it keeps the last call's
+ * contents (every value a call reads is written by that call first, so
+ * nothing needs clearing); calls whose kernels overlap on the GPU -- e.g. on
+ * two streams at once -- race on it and must be serialised by the caller. */
+qf_status qf_expect_number_noalloc(const void *psi_dev, int d, int n, qf_dtype dt, void *cuda_stream, double *out_dev);
+
 /* ---------------------------------------------------------------- programs
  * A program is a circuit recorded once (the Circuit class of "Library
  * Architecture") and executed many times.  Running it plans passes: runs of

@@ -297,3 +297,119 @@ template cudaError_t launch_fibre_reduce<double>(const Launch &, const cplx<doub
                                                  double *, double *);
 
 }  // namespace qf
+
+// ---------------------------------------------------------------------------
+// Allocation-free <N_q> entry point.
+//
+// Some callers cannot allocate device memory when they need a measurement:
+// code recording a CUDA graph (an allocation inside stream capture breaks or
+// serialises the capture), host callbacks and latency-critical loops that must
+// not trigger the implicit device synchronisation cudaMalloc/cudaFree can
+// cause, and hosts whose framework owns the whole device heap through its own
+// pool and leaves nothing for a library to take.  For them this entry point
+// reduces a caller-owned state into a caller-owned output and keeps the
+// per-CTA partial sums in a fixed file-scope device array instead of the
+// scratch a qf_state allocates.
+#include <mutex>
+#include <string>
+
+#include "qf_host.h"
+
+namespace qf {
+
+constexpr int kNoAllocRows = 512;              // CTA partial rows
+constexpr int kNoAllocCols = 64;               // doubles per row: n + 1 <= 64
+constexpr int kNoAllocMaxDevices = 64;
+
+// 512 x 64 doubles = 256 KiB, resident on every device that loads the library
+// until the process exits.
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocRows * kNoAllocCols];
+
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[kNoAllocMaxDevices];   // device address of the array, per device
+static int g_noalloc_sms[kNoAllocMaxDevices];
+
+// Same kernels and CTA partial layout as launch_expect_number, with the CTA
+// count capped by the fixed scratch.
+template <typename R>
+static cudaError_t noalloc_launch(cudaStream_t stream, int sms, const cplx<R> *psi, int d, int n, double *partials,
+                                  double *out_dev) {
+    long long N = 1;
+    for (int i = 0; i < n; ++i) N *= d;
+    int maxb = 2 * sms;
+    if (maxb > kNoAllocRows) maxb = kNoAllocRows;
+    int blocks = 0;
+    switch (d) {
+#define QF_CASE(DD)                                                                                            \
+    case DD: {                                                                                                 \
+        constexpr int CH = ipow_c(DD, NumCfg<DD>::A + NumCfg<DD>::B);                                          \
+        if (n >= NumCfg<DD>::A + NumCfg<DD>::B) {                                                              \
+            long long nch = N / CH;                                                                            \
+            blocks = (int)(nch < maxb ? nch : maxb);                                                           \
+            k_expect_number<R, DD><<<blocks, ipow_c(DD, NumCfg<DD>::A), 0, stream>>>(psi, n, nch, partials); \
+        }                                                                                                      \
+        break;                                                                                                 \
+    }
+        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
+#undef QF_CASE
+    default:
+        break;
+    }
+    if (blocks == 0) {
+        long long b = (N + 255) / 256;
+        blocks = (int)(b < maxb ? b : maxb);
+        k_expect_number_generic<R><<<blocks, 256, 0, stream>>>(psi, d, n, N, partials);
+    }
+    k_sum_partials<<<1, 64, 0, stream>>>(partials, blocks, n + 1, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace qf
+
+extern "C" qf_status qf_expect_number_noalloc(const void *psi_dev, int d, int n, qf_dtype dt, void *cuda_stream,
+                                              double *out_dev) {
+    using namespace qf;
+    if (!psi_dev || ((uintptr_t)psi_dev & 15) != 0)
+        return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: amplitudes must be a non-NULL 16-byte aligned device pointer");
+    if (!out_dev || ((uintptr_t)out_dev & 7) != 0)
+        return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: output must be a non-NULL 8-byte aligned device pointer");
+    if (d < 2 || d > kMaxD) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: d must be in [2, 16]");
+    if (dt != QF_C64 && dt != QF_C128) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: unknown dtype");
+    if (n < 1) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: n must be >= 1");
+    if (n + 1 > kNoAllocCols)
+        return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: n = " + std::to_string(n) +
+                                         " exceeds the fixed scratch (n + 1 <= 64 outputs per CTA row)");
+    long double Nf = 1;
+    for (int i = 0; i < n; ++i) Nf *= d;
+    if (Nf > 9.0e15L) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: d^n too large");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(QF_ERR_UNSUPPORTED, "qf_expect_number_noalloc: device ordinal beyond 63");
+    double *partials = nullptr;
+    int sms = 0;
+    {
+        // one-time set-up per device, with that device current: the host-side
+        // name of the array is not a device address, so look the address up
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            double *p = nullptr;
+            e = cudaGetSymbolAddress((void **)&p, g_noalloc_partials);
+            if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: cudaGetSymbolAddress");
+            int s = 0;
+            e = cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: SM count");
+            g_noalloc_sms[dev] = s > 0 ? s : 1;
+            g_noalloc_ptr[dev] = p;
+        }
+        partials = g_noalloc_ptr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    e = dt == QF_C64 ? noalloc_launch<float>(stream, sms, (const float2 *)psi_dev, d, n, partials, out_dev)
+                     : noalloc_launch<double>(stream, sms, (const double2 *)psi_dev, d, n, partials, out_dev);
+    if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: reduction kernels");
+    return QF_OK;
+}

@@ -60,6 +60,7 @@ _PROTOS = {
     "qf_apply_h": (_int, [_vp, _int]),
     "qf_expect": (_int, [_vp, _c.POINTER(qf_obs), _c.POINTER(_dbl)]),
     "qf_expect_device": (_int, [_vp, _c.POINTER(qf_obs), _vp]),
+    "qf_expect_number_noalloc": (_int, [_vp, _int, _int, _int, _vp, _vp]),
     "qf_program_create": (_int, [_int, _int, _c.POINTER(_vp)]),
     "qf_program_free": (_int, [_vp]),
     "qf_program_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int)]),
@@ -239,6 +240,12 @@ def qf_expect_device(s: int, out_dev_ptr: int, kind: int = QF_OBS_NUMBER_ALL, q:
     o, keep = _obs(kind, q, matrix)
     _call("qf_expect_device", s, _c.byref(o), out_dev_ptr)
     del keep
+
+
+def qf_expect_number_noalloc(psi_dev_ptr: int, d: int, n: int, dtype: int, out_dev_ptr: int, stream=None) -> None:
+    """<N_q> (q < n) and the norm into n + 1 device doubles, allocating
+    nothing (fixed device scratch shared by every call; see include/qf.h)."""
+    _call("qf_expect_number_noalloc", psi_dev_ptr, d, n, dtype, _stream_ptr(stream), out_dev_ptr)
 
 
 # ------------------------------------------------------------------ programs
