@@ -218,6 +218,30 @@ qf_status qf_program_set_fusion(qf_program *p, int enable);
  * at least num_params entries (may be NULL if num_params == 0).  Async. */
 qf_status qf_program_run(qf_program *p, qf_state *s, const double *params);
 
+/* Adjoint gradient (the paper differentiates through stored gate matrices
+ * with autograd, "Sparsity to lower memory consumption"; here the "Generalized rotation
+ * gate" and "Controlled Rotation Gate" definitions U = exp(-i theta G) give
+ * dU/dtheta = -i G U with G = S/2, or sum_m |m><m| (x) m S/2 for the
+ * controlled rotation).  Loss L = sum_q weights[q] <N_q> (weights: n host
+ * doubles).  On entry psi holds the program's output psi_L for `params` (a
+ * qf_program_run of this program on psi_0); lam is a second state of the same
+ * shape and stream used as the costate and overwritten.  The sweep sets
+ * lambda = O psi, then for every gate in reverse adds 2 Im<lambda|G|psi> to
+ * its parameter slot and applies U^+ to psi and lambda; on return psi holds
+ * psi_0 again up to rounding.  Writes L to loss_dev[0] and dL/dparams to
+ * grad_dev[0 .. num_params-1] (device FP64, every slot written, 0 for unused
+ * slots; shared slots sum their gates' terms).  Asynchronous on psi's stream.
+ * Errors: QF_ERR_ARG for mismatched shapes, psi == lam, NULL outputs. */
+qf_status qf_program_adjoint(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
+                             double *loss_dev, double *grad_dev);
+
+/* Forward run of p on psi (holding psi_0 on entry) followed by
+ * qf_program_adjoint; writes the loss and the num_params gradient entries to
+ * host memory and synchronises psi's stream.  psi holds psi_0 again (up to
+ * rounding) on return. */
+qf_status qf_program_gradient(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
+                              double *loss_host, double *grad_host);
+
 /* Number of kernel passes the last run or adjoint launched (for throughput
  * accounting), or -1 before the first run. */
 int qf_program_last_passes(const qf_program *p);

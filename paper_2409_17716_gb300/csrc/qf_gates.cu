@@ -317,7 +317,7 @@ static int fit_rl(const std::vector<bool> &inset, int n, int nt_max, int rl_min)
     return -1;
 }
 
-std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse) {
+std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse, bool for_adjoint) {
     std::vector<PassPlan> plan;
     const int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
     const int rl_min = std::min(min_low_qudits(d), nt_max);
@@ -336,10 +336,12 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
         std::vector<int> last_op_on(n, -1);  // op index touching qudit last
         for (int gi : members) {
             const HGate &g = gates[gi];
-            if (fuse && single_qudit_gate(g) && last_op_on[g.q[0]] >= 0) {
+            // the adjoint needs every parametrised gate as an op of its own
+            const bool mergeable = !for_adjoint || !gate_is_param(g);
+            if (fuse && mergeable && single_qudit_gate(g) && last_op_on[g.q[0]] >= 0) {
                 std::vector<int> &grp = p.groups[last_op_on[g.q[0]]];
                 const HGate &g0 = gates[grp[0]];
-                if (single_qudit_gate(g0)) {
+                if (single_qudit_gate(g0) && (!for_adjoint || !gate_is_param(g0))) {
                     grp.push_back(gi);
                     continue;
                 }
@@ -348,7 +350,7 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
             for (int i = 0; i < g.nq; ++i) last_op_on[g.q[i]] = (int)p.groups.size() - 1;
         }
         // a lone gate on one wide target goes through the strided kernel
-        if (p.groups.size() == 1 && p.groups[0].size() == 1) {
+        if (!for_adjoint && p.groups.size() == 1 && p.groups[0].size() == 1) {
             const HGate &g = gates[p.groups[0][0]];
             int target = (g.kind == G_CROT || g.kind == G_SUM) ? g.q[1] : g.q[0];
             bool strided_ok = (single_qudit_gate(g) && !(g.kind == G_DENSE && g.nq != 1)) || g.kind == G_CROT ||

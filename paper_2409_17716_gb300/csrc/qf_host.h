@@ -27,6 +27,17 @@ template <typename R>
 cudaError_t launch_fibre_reduce(const Launch &L, const cplx<R> *psi, int d, int n, int q, int kind, const double2 *obs_dev,
                                 double *partials, double *out_dev);
 int reduce_max_blocks(int num_sms);
+template <typename R>
+cudaError_t launch_number_obs(const Launch &L, const cplx<R> *psi, cplx<R> *lam, int d, int n, const double *w,
+                              double *partials, double *loss_dev);
+template <typename R>
+cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, int *grid);
+template <typename R>
+cudaError_t launch_tile_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, int d, const TileGeom &g, int nops,
+                            const TOp *ops_dev, const cplx<R> *mat_dev, int nmat, double *rows, int ncols, int grid);
+cudaError_t launch_grad_gather(const Launch &L, const double *rows, const void *terms, const int *first, int nslots,
+                               double *grad);
+size_t gather_term_bytes();
 
 // ---- errors
 qf_status set_error(qf_status s, const std::string &msg);
@@ -85,8 +96,10 @@ int min_low_qudits(int d);                   // rL_min (SEG >= 32)
 long long ipow_ll(int d, int e);
 
 // Plans passes over `gates` (indices into the gate list).  fuse = false gives
-// one pass per gate.
-std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse);
+// one pass per gate.  for_adjoint: tile passes only, and parametrised gates
+// are never multiplied into a group (each needs its own gradient).
+std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse,
+                                  bool for_adjoint = false);
 
 // Tile geometry for the given active qudits and low-qudit count.
 TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);

@@ -108,6 +108,10 @@ struct TOp {
     // divisors by them
     int lsa, lsc;
     FastDiv fa, fc;
+    // adjoint only: column of this op in the pass's gradient row (-1: no
+    // angle) and pool offset of its generator G (dU/dtheta = -i G U), laid out
+    // like the op's matrix (PAIR kinds: 4 entries; DIAG kinds: d entries)
+    int gcol, gmat;
 };
 
 static_assert(sizeof(TOp) % sizeof(int) == 0, "TOp is copied as ints");

@@ -7,6 +7,7 @@
 // the op lists and matrix pools of all passes in one copy, and launches the
 // passes in order on the state's stream.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "qf_host.h"
@@ -36,6 +37,15 @@ struct qf_program {
     std::vector<int> tbefore, tafter;  // event indices around each timed pass
     std::vector<int> tkind;            // 0 tile pass, 1 strided pass
     std::vector<double> tbytes;        // algorithmic HBM bytes of each pass
+    // adjoint
+    bool adj_valid = false;
+    bool adj_c128 = false;
+    std::vector<PassPlan> adj_plan;
+    double *d_rows = nullptr;          // per-CTA gradient rows
+    size_t rows_cap = 0;               // doubles
+    double *d_res = nullptr;           // loss + gradient for the host-result entry point
+    double *h_res = nullptr;
+    size_t res_cap = 0;                // doubles
 };
 
 namespace qf {
@@ -115,6 +125,96 @@ static double strided_bytes(const TOp &o, int d, long long N, int b) {
     return 2.0 * b * fib * rows * frac;
 }
 
+// Copies `host` into the program's device buffer on the state's stream (after
+// every earlier use of the buffer by this program on any stream).
+static qf_status upload(qf_program *p, qf_state *s, const std::vector<unsigned char> &host) {
+    if (p->up_pending) {
+        QF_CUDA(cudaEventSynchronize(p->up_ev));
+        p->up_pending = false;
+    }
+    if (p->ran) QF_CUDA(cudaStreamWaitEvent(s->stream, p->done_ev, 0));
+    if (host.size() > p->cap) {
+        if (p->ran) QF_CUDA(cudaEventSynchronize(p->done_ev));
+        if (p->h_buf) cudaFreeHost(p->h_buf);
+        if (p->d_buf) cudaFree(p->d_buf);
+        p->h_buf = p->d_buf = nullptr;
+        p->cap = 0;
+        size_t cap = align16(host.size() + host.size() / 2 + 1024);
+        if (cudaMallocHost(&p->h_buf, cap) != cudaSuccess || cudaMalloc(&p->d_buf, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "program buffer allocation failed");
+        }
+        p->cap = cap;
+    }
+    if (!host.empty()) {
+        std::memcpy(p->h_buf, host.data(), host.size());
+        QF_CUDA(cudaMemcpyAsync(p->d_buf, p->h_buf, host.size(), cudaMemcpyHostToDevice, s->stream));
+        QF_CUDA(cudaEventRecord(p->up_ev, s->stream));
+        p->up_pending = true;
+    }
+    return QF_OK;
+}
+
+// U^+ of a resolved op, in the same op layout.
+static ROp dagger(const ROp &r, int d) {
+    ROp o = r;
+    auto cj = [](const cd &z) { return std::conj(z); };
+    switch (r.op.kind) {
+    case OP_DENSE:
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) o.m[a * d + b] = cj(r.m[b * d + a]);
+        break;
+    case OP_PAIR:
+        o.m[0] = cj(r.m[0]); o.m[1] = cj(r.m[2]); o.m[2] = cj(r.m[1]); o.m[3] = cj(r.m[3]);
+        break;
+    case OP_CPAIR:
+        for (int m = 0; m < d; ++m) {
+            const cd *src = r.m.data() + 4 * m;
+            cd *dst = o.m.data() + 4 * m;
+            dst[0] = cj(src[0]); dst[1] = cj(src[2]); dst[2] = cj(src[1]); dst[3] = cj(src[3]);
+        }
+        break;
+    case OP_DIAG:
+    case OP_CDIAG:
+        for (auto &z : o.m) z = cj(z);
+        break;
+    case OP_SHIFT:
+    case OP_CSHIFT:
+        o.op.s = (d - r.op.s % d) % d;
+        break;
+    case OP_DENSEK: {
+        int K = (int)std::lround(std::sqrt((double)r.m.size()));
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) o.m[a * K + b] = cj(r.m[b * K + a]);
+        break;
+    }
+    default:  // SWAP is its own inverse
+        break;
+    }
+    return o;
+}
+
+// Generator G = S/2 of a parametrised gate (dU/dtheta = -i G U), in the layout
+// of the op's matrix: PAIR kinds (jj, jk, kj, kk), DIAG kinds d real entries.
+static std::vector<cd> generator_entries(const HGate &g, int d) {
+    std::vector<cd> G;
+    if (g.axis == 'x') {
+        G = {cd(0, 0), cd(0.5, 0), cd(0.5, 0), cd(0, 0)};
+    } else if (g.axis == 'y') {
+        G = {cd(0, 0), cd(0, -0.5), cd(0, 0.5), cd(0, 0)};
+    } else if (g.axis == 'z') {
+        G.assign(d, cd(0, 0));
+        G[g.j] = cd(0.5, 0);
+        G[g.k] = cd(-0.5, 0);
+    } else {  // 'g'
+        G.assign(d, cd(0, 0));
+        const double gam = std::sqrt(2.0 / ((double)g.j * (double)(g.j + 1)));
+        for (int l = 0; l < g.j; ++l) G[l] = cd(0.5 * gam, 0);
+        G[g.j] = cd(-0.5 * g.j * gam, 0);
+    }
+    return G;
+}
+
 template <typename R>
 static qf_status run_program_t(qf_program *p, qf_state *s, const double *params) {
     using C = cplx<R>;
@@ -159,31 +259,8 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         std::memcpy(host.data() + b.off, pool.data(), pool.size() * sizeof(C));
         std::memcpy(host.data() + b.off + align16(pool.size() * sizeof(C)), ops.data(), ops.size() * sizeof(TOp));
     }
-    // upload
-    if (p->up_pending) {
-        QF_CUDA(cudaEventSynchronize(p->up_ev));
-        p->up_pending = false;
-    }
-    if (p->ran) QF_CUDA(cudaStreamWaitEvent(s->stream, p->done_ev, 0));
-    if (host.size() > p->cap) {
-        if (p->ran) QF_CUDA(cudaEventSynchronize(p->done_ev));
-        if (p->h_buf) cudaFreeHost(p->h_buf);
-        if (p->d_buf) cudaFree(p->d_buf);
-        p->h_buf = p->d_buf = nullptr;
-        p->cap = 0;
-        size_t cap = align16(host.size() + host.size() / 2 + 1024);
-        if (cudaMallocHost(&p->h_buf, cap) != cudaSuccess || cudaMalloc(&p->d_buf, cap) != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(QF_ERR_OOM, "program buffer allocation failed");
-        }
-        p->cap = cap;
-    }
-    if (!host.empty()) {
-        std::memcpy(p->h_buf, host.data(), host.size());
-        QF_CUDA(cudaMemcpyAsync(p->d_buf, p->h_buf, host.size(), cudaMemcpyHostToDevice, s->stream));
-        QF_CUDA(cudaEventRecord(p->up_ev, s->stream));
-        p->up_pending = true;
-    }
+    qf_status ust = upload(p, s, host);
+    if (ust != QF_OK) return ust;
     Launch L;
     L.stream = s->stream;
     L.num_sms = s->num_sms;
@@ -241,6 +318,131 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
     return QF_OK;
 }
 
+template <typename R>
+static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
+                               double *loss_dev, double *grad_dev) {
+    using C = cplx<R>;
+    const int d = p->d, n = p->n;
+    const bool c128 = sizeof(R) == 8;
+    if (!p->adj_valid || p->adj_c128 != c128) {
+        p->adj_plan = plan_passes(p->gates, d, n, c128, p->fuse, true);
+        p->adj_valid = true;
+        p->adj_c128 = c128;
+    }
+    const auto &plan = p->adj_plan;
+    const int np = (int)plan.size();
+    struct Built {
+        size_t off = 0;
+        int nops = 0, nmat = 0, ncols = 0, grid = 0;
+        long long rows_base = 0;
+    };
+    std::vector<Built> built(np);
+    std::vector<unsigned char> host;
+    // gradient terms per slot: (pass in execution order, column)
+    std::vector<std::vector<std::pair<int, int>>> terms(p->num_params);
+    long long rows_total = 0;
+    for (int k = 0; k < np; ++k) {
+        const PassPlan &pp = plan[np - 1 - k];   // execution order: last pass first
+        Built &b = built[k];
+        std::vector<TOp> ops;
+        std::vector<C> pool;
+        int ncols = 0;
+        for (int gi = (int)pp.groups.size() - 1; gi >= 0; --gi) {
+            const auto &grp = pp.groups[gi];
+            ROp r = dagger(resolve_group(p->gates, grp, d, params), d);
+            TOp o = localize(r.op, pp.geom, pp.active, n, d);
+            o.mat = (int)pool.size();
+            for (const cd &z : r.m) pool.push_back(mk<R>((R)z.real(), (R)z.imag()));
+            o.gcol = -1;
+            o.gmat = 0;
+            const HGate &g0 = p->gates[grp[0]];
+            if (grp.size() == 1 && gate_is_param(g0)) {
+                o.gcol = ncols++;
+                o.gmat = (int)pool.size();
+                for (const cd &z : generator_entries(g0, d)) pool.push_back(mk<R>((R)z.real(), (R)z.imag()));
+                terms[g0.slot].push_back({k, o.gcol});
+            }
+            ops.push_back(o);
+        }
+        b.nops = (int)ops.size();
+        b.nmat = (int)pool.size();
+        b.ncols = ncols;
+        cudaError_t e = adj_grid<R>(psi->num_sms, d, pp.geom, b.nops, b.nmat, &b.grid);
+        if (e != cudaSuccess) return cuda_error(e, "adjoint pass occupancy");
+        b.rows_base = rows_total;
+        rows_total += (long long)b.grid * ncols;
+        b.off = align16(host.size());
+        host.resize(b.off + align16(pool.size() * sizeof(C)) + ops.size() * sizeof(TOp));
+        std::memcpy(host.data() + b.off, pool.data(), pool.size() * sizeof(C));
+        std::memcpy(host.data() + b.off + align16(pool.size() * sizeof(C)), ops.data(), ops.size() * sizeof(TOp));
+    }
+    // gather table
+    const size_t tb = gather_term_bytes();
+    std::vector<unsigned char> tbuf;
+    std::vector<int> first(p->num_params + 1, 0);
+    for (int sl = 0; sl < p->num_params; ++sl) {
+        first[sl + 1] = first[sl] + (int)terms[sl].size();
+        for (auto &t : terms[sl]) {
+            const Built &b = built[t.first];
+            struct {
+                long long base;
+                int nrows, ncols, col, pad;
+            } rec = {b.rows_base, b.grid, b.ncols, t.second, 0};
+            static_assert(sizeof(rec) == 24, "gather term layout");
+            size_t at = tbuf.size();
+            tbuf.resize(at + tb);
+            std::memcpy(tbuf.data() + at, &rec, sizeof(rec));
+        }
+    }
+    const size_t terms_off = align16(host.size());
+    host.resize(terms_off + tbuf.size());
+    if (!tbuf.empty()) std::memcpy(host.data() + terms_off, tbuf.data(), tbuf.size());
+    const size_t first_off = align16(host.size());
+    host.resize(first_off + first.size() * sizeof(int));
+    std::memcpy(host.data() + first_off, first.data(), first.size() * sizeof(int));
+
+    // gradient rows scratch
+    if ((size_t)rows_total > p->rows_cap) {
+        if (p->ran) QF_CUDA(cudaEventSynchronize(p->done_ev));
+        if (p->d_rows) cudaFree(p->d_rows);
+        p->d_rows = nullptr;
+        p->rows_cap = 0;
+        size_t cap = (size_t)rows_total + 1024;
+        if (cudaMalloc(&p->d_rows, cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "gradient scratch allocation failed");
+        }
+        p->rows_cap = cap;
+    }
+    qf_status st = upload(p, psi, host);
+    if (st != QF_OK) return st;
+    if (lam->stream != psi->stream) return set_error(QF_ERR_ARG, "psi and lambda must share a stream");
+
+    Launch L;
+    L.stream = psi->stream;
+    L.num_sms = psi->num_sms;
+    C *ps = reinterpret_cast<C *>(psi->data);
+    C *ls = reinterpret_cast<C *>(lam->data);
+    cudaError_t e = launch_number_obs<R>(L, ps, ls, d, n, weights, psi->d_partials, loss_dev);
+    if (e != cudaSuccess) return cuda_error(e, "lambda = O psi");
+    const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
+    for (int k = 0; k < np; ++k) {
+        const PassPlan &pp = plan[np - 1 - k];
+        const Built &b = built[k];
+        const C *pool = reinterpret_cast<const C *>(dev + b.off);
+        const TOp *ops = reinterpret_cast<const TOp *>(dev + b.off + align16(b.nmat * sizeof(C)));
+        e = launch_tile_adj<R>(L, ps, ls, d, pp.geom, b.nops, ops, pool, b.nmat, p->d_rows + b.rows_base, b.ncols, b.grid);
+        if (e != cudaSuccess) return cuda_error(e, "adjoint pass");
+    }
+    e = launch_grad_gather(L, p->d_rows, dev + terms_off, reinterpret_cast<const int *>(dev + first_off), p->num_params,
+                           grad_dev);
+    if (e != cudaSuccess) return cuda_error(e, "gradient gather");
+    QF_CUDA(cudaEventRecord(p->done_ev, psi->stream));
+    p->ran = true;
+    p->last_passes = np;
+    return QF_OK;
+}
+
 }  // namespace qf
 
 extern "C" {
@@ -263,6 +465,9 @@ qf_status qf_program_free(qf_program *p) {
     if (p->h_buf) cudaFreeHost(p->h_buf);
     if (p->d_buf) cudaFree(p->d_buf);
     for (cudaEvent_t ev : p->tev) cudaEventDestroy(ev);
+    if (p->d_rows) cudaFree(p->d_rows);
+    if (p->d_res) cudaFree(p->d_res);
+    if (p->h_res) cudaFreeHost(p->h_res);
     if (p->up_ev) cudaEventDestroy(p->up_ev);
     if (p->done_ev) cudaEventDestroy(p->done_ev);
     delete p;
@@ -283,6 +488,7 @@ static qf_status add(qf_program *p, HGate g) {
     if (g.slot >= 0 && g.slot + 1 > p->num_params) p->num_params = g.slot + 1;
     p->gates.push_back(std::move(g));
     p->plan_valid = false;
+    p->adj_valid = false;
     return QF_OK;
 }
 
@@ -344,6 +550,7 @@ qf_status qf_program_set_fusion(qf_program *p, int enable) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     p->fuse = enable != 0;
     p->plan_valid = false;
+    p->adj_valid = false;
     return QF_OK;
 }
 
@@ -381,6 +588,61 @@ qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_
     if (num_passes) *num_passes = (int)p->plan.size();
     if (num_strided) *num_strided = ns;
     if (max_ops) *max_ops = mo;
+    return QF_OK;
+}
+
+static qf_status ensure_events(qf_program *p) {
+    if (!p->up_ev) {
+        if (cudaEventCreateWithFlags(&p->up_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_CUDA, "event creation failed");
+        }
+    }
+    return QF_OK;
+}
+
+qf_status qf_program_adjoint(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
+                             double *loss_dev, double *grad_dev) {
+    if (!p || !psi || !lam) return set_error(QF_ERR_ARG, "program or state is NULL");
+    if (psi == lam || psi->data == lam->data) return set_error(QF_ERR_ARG, "psi and lambda must be different states");
+    if (p->d != psi->d || p->n != psi->n || lam->d != psi->d || lam->n != psi->n || lam->dt != psi->dt)
+        return set_error(QF_ERR_ARG, "program and state sizes differ");
+    if (!weights) return set_error(QF_ERR_ARG, "weights are NULL");
+    if (!loss_dev || !grad_dev) return set_error(QF_ERR_ARG, "outputs are NULL");
+    if (p->num_params > 0 && !params) return set_error(QF_ERR_ARG, "program needs parameters");
+    qf_status st = ensure_events(p);
+    if (st != QF_OK) return st;
+    return psi->dt == QF_C64 ? run_adjoint_t<float>(p, psi, lam, params, weights, loss_dev, grad_dev)
+                             : run_adjoint_t<double>(p, psi, lam, params, weights, loss_dev, grad_dev);
+}
+
+qf_status qf_program_gradient(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
+                              double *loss_host, double *grad_host) {
+    if (!p || !psi || !lam) return set_error(QF_ERR_ARG, "program or state is NULL");
+    if (!loss_host || (p->num_params > 0 && !grad_host)) return set_error(QF_ERR_ARG, "outputs are NULL");
+    const size_t need = (size_t)p->num_params + 1;
+    if (need > p->res_cap) {
+        if (p->d_res) { cudaStreamSynchronize(psi->stream); cudaFree(p->d_res); }
+        if (p->h_res) cudaFreeHost(p->h_res);
+        p->d_res = nullptr;
+        p->h_res = nullptr;
+        p->res_cap = 0;
+        if (cudaMalloc(&p->d_res, need * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&p->h_res, need * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "gradient result allocation failed");
+        }
+        p->res_cap = need;
+    }
+    qf_status st = qf_program_run(p, psi, params);
+    if (st != QF_OK) return st;
+    st = qf_program_adjoint(p, psi, lam, params, weights, p->d_res, p->d_res + 1);
+    if (st != QF_OK) return st;
+    QF_CUDA(cudaMemcpyAsync(p->h_res, p->d_res, need * sizeof(double), cudaMemcpyDeviceToHost, psi->stream));
+    QF_CUDA(cudaStreamSynchronize(psi->stream));
+    *loss_host = p->h_res[0];
+    if (p->num_params > 0) std::memcpy(grad_host, p->h_res + 1, p->num_params * sizeof(double));
     return QF_OK;
 }
 

@@ -76,6 +76,9 @@ _PROTOS = {
     "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
     "qf_program_last_passes": (_int, [_vp]),
     "qf_program_plan": (_int, [_vp, _int, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
+    "qf_program_adjoint": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _vp, _vp]),
+    "qf_program_gradient": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _c.POINTER(_dbl),
+                                   _c.POINTER(_dbl)]),
     "qf_program_set_timing": (_int, [_vp, _int]),
     "qf_program_pass_times": (_int, [_vp, _int, _c.POINTER(_c.c_float), _c.POINTER(_int), _c.POINTER(_dbl),
                                      _c.POINTER(_int)]),
@@ -312,6 +315,29 @@ def qf_program_run(p: int, s: int, params=None) -> None:
         _call("qf_program_run", p, s, _dptr(a))
 
 
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def qf_program_adjoint(p: int, psi: int, lam: int, params, weights, loss_dev_ptr: int, grad_dev_ptr: int) -> None:
+    """Reverse sweep from psi_L (in psi) to psi_0; loss and gradient to device
+    FP64 buffers (asynchronous)."""
+    pa = _f64(params if params is not None else [0.0])
+    w = _f64(weights)
+    _call("qf_program_adjoint", p, psi, lam, _dptr(pa), _dptr(w), loss_dev_ptr, grad_dev_ptr)
+
+
+def qf_program_gradient(p: int, psi: int, lam: int, params, weights):
+    """Forward + adjoint from psi_0 (in psi); returns (loss, gradient) on the host."""
+    pa = _f64(params if params is not None else [0.0])
+    w = _f64(weights)
+    _, P = qf_program_info(p)
+    g = np.zeros(max(P, 1))
+    loss = np.zeros(1)
+    _call("qf_program_gradient", p, psi, lam, _dptr(pa), _dptr(w), _dptr(loss), _dptr(g))
+    return float(loss[0]), g[:P]
+
+
 def qf_program_last_passes(p: int) -> int:
     return lib().qf_program_last_passes(p)
 
@@ -425,3 +451,71 @@ def program_from_ops(d: int, n: int, ops: Iterable, fuse: bool = True) -> int:
             raise ValueError(k)
     qf_program_set_fusion(p, fuse)
     return p
+
+
+class Expectation:
+    """<N_q> of a program's output as a differentiable torch function of its
+    parameters: forward runs the program on a copy of psi_0 and reduces
+    <N_q> (q < n) with qf_expect_device; backward takes dL/d<N_q> as the
+    observable weights and runs the adjoint sweep (qf_program_adjoint) on the
+    saved output state.  Each forward supports one backward."""
+
+    def __init__(self, d: int, n: int, ops, dtype: str = "c64"):
+        self.d, self.n, self.dtype = d, n, dtype
+        self.program = program_from_ops(d, n, ops)
+        self.num_params = qf_program_info(self.program)[1]
+        self.psi = State(d, n, dtype)
+        self.lam = State(d, n, dtype)
+
+    def __call__(self, params, psi0=None):
+        import torch
+        return _ExpectationFn.apply(params, self, psi0)
+
+    def free(self):
+        qf_program_free(self.program)
+        self.psi.free()
+        self.lam.free()
+
+
+def _expectation_fn():
+    import torch
+
+    class Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, ex, psi0):
+            p_host = params.detach().to("cpu", torch.float64).numpy()
+            if psi0 is None:
+                ex.psi.set_basis(0)
+            else:
+                ex.psi.tensor.copy_(psi0)
+            qf_program_run(ex.program, ex.psi.handle, p_host)
+            out = torch.zeros(ex.n + 1, dtype=torch.float64, device="cuda")
+            qf_expect_device(ex.psi.handle, out.data_ptr(), QF_OBS_NUMBER_ALL)
+            ctx.ex = ex
+            ctx.p_host = p_host
+            ctx.param_device = params.device
+            return out[: ex.n].clone()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            ex = ctx.ex
+            w = grad_out.detach().to("cpu", torch.float64).numpy()
+            loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            grad = torch.zeros(max(ex.num_params, 1), dtype=torch.float64, device="cuda")
+            qf_program_adjoint(ex.program, ex.psi.handle, ex.lam.handle, ctx.p_host, w, loss.data_ptr(),
+                               grad.data_ptr())
+            return grad[: ex.num_params].to(ctx.param_device), None, None
+
+    return Fn
+
+
+class _LazyFn:
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFn._fn is None:
+            _LazyFn._fn = _expectation_fn()
+        return _LazyFn._fn.apply(*args)
+
+
+_ExpectationFn = _LazyFn()
