@@ -266,6 +266,67 @@ qf_status qf_program_pass_times(qf_program *p, int max, float *ms, int *kind, do
  * and the largest number of ops in one pass.  Output pointers may be NULL. */
 qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_strided, int *max_ops);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent circuits of uneven qudit dimension and size (the
+ * data-encoding VQA circuits of the paper's "Variational quantum algorithm"
+ * section, one per sample), run forward and backward together.  Each circuit
+ * is a recorded program whose parametrised gates index one global parameter
+ * vector (shared trainable angles and per-sample encoding angles alike) and a
+ * loss L_c = sum_q weights_c[q] <N_q> on its own output.  Every circuit starts
+ * from |0...0>.  Building plans each distinct circuit structure once, lays out
+ * a psi and a lambda state per circuit in one device allocation, and captures
+ * the whole run -- initialisation, one batched tile launch
+ * per (qudit dimension, pass index), lambda = O psi with the losses, the
+ * reverse passes and the gradient gathers -- into a CUDA graph; qf_batch_run
+ * uploads the parameters and replays it.  Rotation entries are computed on the device from the
+ * parameters, so the graph is valid for every parameter vector. */
+typedef struct qf_batch qf_batch;
+
+qf_status qf_batch_create(qf_dtype dt, void *cuda_stream, qf_batch **out);
+qf_status qf_batch_free(qf_batch *b);
+
+/* Copies the program's gates and n loss weights into the batch (before
+ * qf_batch_build).  *index receives the circuit's index.  Circuits need
+ * d^n < 2^31. */
+qf_status qf_batch_add(qf_batch *b, const qf_program *p, const double *weights, int *index);
+
+/* Tile size (local qudits, 0 = default) and fusion depth (gates per pass,
+ * 0 = default) for the circuits of qudit dimension d; before building. */
+qf_status qf_batch_tune(qf_batch *b, int d, int tile_qudits, int max_ops);
+
+/* Plans, allocates (2 states per circuit plus tables) and captures the
+ * graphs.  num_params = length of the global parameter vector; every slot a
+ * circuit uses must be below it. */
+qf_status qf_batch_build(qf_batch *b, int num_params);
+
+/* Runs the batch for the host parameter vector (copied at the call, so the
+ * caller may reuse it at once).  backward = 0: losses only; backward = 1:
+ * losses and gradients.  Asynchronous with respect to the stream given at
+ * creation (the batch runs on its own stream ordered after it). */
+qf_status qf_batch_run(qf_batch *b, const double *params, int backward);
+
+/* Device FP64 outputs of the last run, owned by the batch: loss[c] per
+ * circuit; grad_local: for circuit c, at its grad_offset, dL_c/dparam for
+ * each slot it uses (ascending slot order, see qf_batch_circuit_params);
+ * grad_sum[s] = sum over circuits of dL_c/dparam_s. */
+qf_status qf_batch_outputs(qf_batch *b, double **loss_dev, double **grad_local_dev, double **grad_sum_dev);
+
+/* Copies the last run's outputs to host memory after waiting for it: loss
+ * (one per circuit), grad_local and grad_sum with the lengths qf_batch_info
+ * reports.  Any pointer may be NULL. */
+qf_status qf_batch_read(qf_batch *b, double *loss_host, double *grad_local_host, double *grad_sum_host);
+
+/* Parameter slots circuit `index` uses (ascending, up to max written), their
+ * count and the offset of its entries in grad_local. */
+qf_status qf_batch_circuit_params(const qf_batch *b, int index, int *slots, int max, int *count, long long *grad_offset);
+
+/* Circuits, total amplitudes, sum over circuits of amplitudes x gates, the
+ * kernel launches one forward-only / forward+backward graph replay makes, the
+ * length of grad_local and of the parameter vector (grad_sum).  Any output
+ * pointer may be NULL. */
+qf_status qf_batch_info(const qf_batch *b, int *circuits, long long *amplitudes, double *gate_amplitudes,
+                        int *launches_forward, int *launches_backward, long long *grad_local_len, int *num_params);
+
 #ifdef __cplusplus
 }
 #endif

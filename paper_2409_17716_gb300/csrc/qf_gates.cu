@@ -317,9 +317,12 @@ static int fit_rl(const std::vector<bool> &inset, int n, int nt_max, int rl_min)
     return -1;
 }
 
-std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse, bool for_adjoint) {
+std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse, bool for_adjoint,
+                                  int nt_override, int max_ops) {
     std::vector<PassPlan> plan;
-    const int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
+    int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
+    if (nt_override > 0 && nt_override < nt_max) nt_max = nt_override;
+    const int op_cap = (max_ops > 0 && max_ops < kMaxTileOps) ? max_ops : kMaxTileOps;
     const int rl_min = std::min(min_low_qudits(d), nt_max);
     std::vector<int> remaining(gates.size());
     for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
@@ -376,7 +379,7 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
             bool is_blocked = false;
             for (int q : qs) is_blocked |= blocked[q];
             bool take = false;
-            if (!is_blocked && (int)members.size() < kMaxTileOps && (fuse || members.empty())) {
+            if (!is_blocked && (int)members.size() < op_cap && (fuse || members.empty())) {
                 std::vector<bool> trial = inset;
                 for (int q : qs) trial[q] = true;
                 if (fit_rl(trial, n, nt_max, rl_min) >= 0) {

@@ -99,7 +99,7 @@ long long ipow_ll(int d, int e);
 // one pass per gate.  for_adjoint: tile passes only, and parametrised gates
 // are never multiplied into a group (each needs its own gradient).
 std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse,
-                                  bool for_adjoint = false);
+                                  bool for_adjoint = false, int nt_override = 0, int max_ops = 0);
 
 // Tile geometry for the given active qudits and low-qudit count.
 TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);
@@ -107,6 +107,10 @@ TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);
 int local_pos(const TileGeom &g, const std::vector<int> &active, int n, int q);
 // Converts a resolved op on global qudits into tile-local form.
 TOp localize(const TOp &op, const TileGeom &g, const std::vector<int> &active, int n, int d);
+
+// Shape and recorded gates of a program (for batches).
+qf_status program_shape(const qf_program *p, int *d, int *n);
+qf_status program_gates(const qf_program *p, std::vector<HGate> *out);
 
 }  // namespace qf
 

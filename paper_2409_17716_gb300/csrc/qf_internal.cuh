@@ -112,6 +112,11 @@ struct TOp {
     // angle) and pool offset of its generator G (dU/dtheta = -i G U), laid out
     // like the op's matrix (PAIR kinds: 4 entries; DIAG kinds: d entries)
     int gcol, gmat;
+    // batched programs only: rotation angle taken on the device from the
+    // parameter vector (pslot >= 0), entries written into the pool at `mat`;
+    // paxis = 'x','y','z','g'; psign = +1 forward, -1 adjoint (R(theta)^+ =
+    // R(-theta))
+    int pslot, paxis, psign;
 };
 
 static_assert(sizeof(TOp) % sizeof(int) == 0, "TOp is copied as ints");

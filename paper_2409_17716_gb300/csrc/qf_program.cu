@@ -443,6 +443,19 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     return QF_OK;
 }
 
+qf_status program_shape(const qf_program *p, int *d, int *n) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    *d = p->d;
+    *n = p->n;
+    return QF_OK;
+}
+
+qf_status program_gates(const qf_program *p, std::vector<HGate> *out) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    *out = p->gates;
+    return QF_OK;
+}
+
 }  // namespace qf
 
 extern "C" {

@@ -79,6 +79,18 @@ _PROTOS = {
     "qf_program_adjoint": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _vp, _vp]),
     "qf_program_gradient": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _c.POINTER(_dbl),
                                    _c.POINTER(_dbl)]),
+    "qf_batch_create": (_int, [_int, _vp, _c.POINTER(_vp)]),
+    "qf_batch_free": (_int, [_vp]),
+    "qf_batch_add": (_int, [_vp, _vp, _c.POINTER(_dbl), _c.POINTER(_int)]),
+    "qf_batch_tune": (_int, [_vp, _int, _int, _int]),
+    "qf_batch_build": (_int, [_vp, _int]),
+    "qf_batch_run": (_int, [_vp, _c.POINTER(_dbl), _int]),
+    "qf_batch_outputs": (_int, [_vp, _c.POINTER(_vp), _c.POINTER(_vp), _c.POINTER(_vp)]),
+    "qf_batch_circuit_params": (_int, [_vp, _int, _c.POINTER(_int), _int, _c.POINTER(_int),
+                                       _c.POINTER(_c.c_longlong)]),
+    "qf_batch_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_c.c_longlong), _c.POINTER(_dbl), _c.POINTER(_int),
+                             _c.POINTER(_int), _c.POINTER(_c.c_longlong), _c.POINTER(_int)]),
+    "qf_batch_read": (_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _c.POINTER(_dbl)]),
     "qf_program_set_timing": (_int, [_vp, _int]),
     "qf_program_pass_times": (_int, [_vp, _int, _c.POINTER(_c.c_float), _c.POINTER(_int), _c.POINTER(_dbl),
                                      _c.POINTER(_int)]),
@@ -336,6 +348,72 @@ def qf_program_gradient(p: int, psi: int, lam: int, params, weights):
     loss = np.zeros(1)
     _call("qf_program_gradient", p, psi, lam, _dptr(pa), _dptr(w), _dptr(loss), _dptr(g))
     return float(loss[0]), g[:P]
+
+
+def qf_batch_create(dtype: int = QF_C64, stream=None) -> int:
+    h = _vp()
+    _call("qf_batch_create", dtype, _stream_ptr(stream), _c.byref(h))
+    return h.value
+
+
+def qf_batch_free(b: int) -> None:
+    _call("qf_batch_free", b)
+
+
+def qf_batch_add(b: int, p: int, weights) -> int:
+    w = _f64(weights)
+    idx = _int()
+    _call("qf_batch_add", b, p, _dptr(w), _c.byref(idx))
+    return idx.value
+
+
+def qf_batch_tune(b: int, d: int, tile_qudits: int = 0, max_ops: int = 0) -> None:
+    _call("qf_batch_tune", b, d, tile_qudits, max_ops)
+
+
+def qf_batch_build(b: int, num_params: int) -> None:
+    _call("qf_batch_build", b, int(num_params))
+
+
+def qf_batch_run(b: int, params, backward: bool = True) -> None:
+    pa = _f64(params if params is not None else [0.0])
+    _call("qf_batch_run", b, _dptr(pa), 1 if backward else 0)
+
+
+def qf_batch_outputs(b: int):
+    """Device pointers (loss, grad_local, grad_sum)."""
+    a, g, s = _vp(), _vp(), _vp()
+    _call("qf_batch_outputs", b, _c.byref(a), _c.byref(g), _c.byref(s))
+    return a.value, g.value, s.value
+
+
+def qf_batch_circuit_params(b: int, index: int):
+    """(slots, grad_offset) of circuit `index`."""
+    cnt, off = _int(), _c.c_longlong()
+    _call("qf_batch_circuit_params", b, index, None, 0, _c.byref(cnt), _c.byref(off))
+    slots = (_int * max(cnt.value, 1))()
+    _call("qf_batch_circuit_params", b, index, slots, cnt.value, _c.byref(cnt), _c.byref(off))
+    return [slots[i] for i in range(cnt.value)], off.value
+
+
+def qf_batch_info(b: int):
+    c, a, ga, lf, lb, gl, npar = _int(), _c.c_longlong(), _dbl(), _int(), _int(), _c.c_longlong(), _int()
+    _call("qf_batch_info", b, _c.byref(c), _c.byref(a), _c.byref(ga), _c.byref(lf), _c.byref(lb), _c.byref(gl),
+          _c.byref(npar))
+    return {"circuits": c.value, "amplitudes": a.value, "gate_amplitudes": ga.value,
+            "launches_forward": lf.value, "launches_backward": lb.value, "grad_local_len": gl.value,
+            "num_params": npar.value}
+
+
+def qf_batch_read(b: int):
+    """Host copies (loss per circuit, grad_local, grad_sum) of the last run;
+    every buffer is sized from the batch itself."""
+    info = qf_batch_info(b)
+    loss = np.zeros(max(info["circuits"], 1))
+    gl = np.zeros(max(info["grad_local_len"], 1))
+    gs = np.zeros(max(info["num_params"], 1))
+    _call("qf_batch_read", b, _dptr(loss), _dptr(gl), _dptr(gs))
+    return loss[:info["circuits"]], gl[:info["grad_local_len"]], gs[:info["num_params"]]
 
 
 def qf_program_last_passes(p: int) -> int:

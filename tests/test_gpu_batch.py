@@ -1,0 +1,118 @@
+"""GPU parity of the batched forward and adjoint (qf_batch_*).
+
+An uneven batch (d in 2..5, n in 4..10 or smaller, 2..6 layers; Fourier +
+per-sample RZ encoding + shared-angle ansatz; loss <N_0>) is built once and run
+through the captured graph.  Every circuit's loss and local gradient is
+compared with the same circuit run alone through qf_program_gradient, a subset
+of small circuits with the oracle (brute-force derivative circuits), and the
+summed gradient with the sum of the per-circuit gradients.  A second run with
+new parameters checks that the graph follows the parameter vector.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_lib
+from paper_2409_17716_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(qf, circuits, params, dtype, weights_fn):
+    b = qf.qf_batch_create(qf.QF_C64 if dtype == "c64" else qf.QF_C128)
+    progs = []
+    for c in circuits:
+        p = qf.program_from_ops(c.d, c.n, c.ops)
+        qf.qf_batch_add(b, p, weights_fn(c))
+        progs.append(p)
+    qf.qf_batch_build(b, len(params))
+    return b, progs
+
+
+def outputs(qf, b, ncirc, nlocal, nparams):
+    loss, gl, gs = qf.qf_batch_read(b)
+    assert len(loss) == ncirc
+    return loss, gl, gs
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_batch_matches_single_circuits(orc, dtype):
+    qf = gpu_lib()
+    circuits, params = W.batch_circuits(count=48, seed=123, n_range=(2, 7))
+    w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
+    b, progs = make_batch(qf, circuits, params, dtype, w0)
+    qf.qf_batch_run(b, params, True)
+    info = qf.qf_batch_info(b)
+    nlocal = sum(len(qf.qf_batch_circuit_params(b, i)[0]) for i in range(len(circuits)))
+    loss, gl, gs = outputs(qf, b, len(circuits), nlocal, len(params))
+    tol_l = 1e-12 if dtype == "c128" else 2e-6
+    tol_g = 1e-10 if dtype == "c128" else 2e-5
+    gsum = np.zeros(len(params))
+    for i, c in enumerate(circuits):
+        slots, off = qf.qf_batch_circuit_params(b, i)
+        g_i = gl[off:off + len(slots)]
+        gsum[slots] += g_i
+        psi = qf.State(c.d, c.n, dtype)
+        psi.set_basis(0)
+        lam = qf.State(c.d, c.n, dtype)
+        l1, g1 = qf.qf_program_gradient(progs[i], psi.handle, lam.handle, params, w0(c))
+        psi.free()
+        lam.free()
+        assert abs(loss[i] - l1) <= tol_l, (i, loss[i], l1)
+        assert np.abs(g_i - g1[slots]).max() <= tol_g, (i, np.abs(g_i - g1[slots]).max())
+        if c.d ** c.n <= 800 and i % 3 == 0:
+            want = orc.grad_bruteforce(c.ops, c.d, c.n, params, w0(c), slots=slots)
+            assert np.abs(g_i - want).max() <= tol_g
+            wl = orc.loss(orc.run(c.ops, c.d, c.n, params=params), c.d, c.n, w0(c))
+            assert abs(loss[i] - wl) <= tol_l
+    np.testing.assert_allclose(gs, gsum, atol=1e-12 * max(1, len(circuits)))
+    # new parameters: the captured graph must follow them
+    p2 = params + 0.37
+    qf.qf_batch_run(b, p2, True)
+    loss2, gl2, _ = outputs(qf, b, len(circuits), nlocal, len(params))
+    for i in (0, len(circuits) // 2, len(circuits) - 1):
+        c = circuits[i]
+        slots, off = qf.qf_batch_circuit_params(b, i)
+        psi = qf.State(c.d, c.n, dtype)
+        psi.set_basis(0)
+        lam = qf.State(c.d, c.n, dtype)
+        l1, g1 = qf.qf_program_gradient(progs[i], psi.handle, lam.handle, p2, w0(c))
+        psi.free()
+        lam.free()
+        assert abs(loss2[i] - l1) <= tol_l
+        assert np.abs(gl2[off:off + len(slots)] - g1[slots]).max() <= tol_g
+    # forward only
+    qf.qf_batch_run(b, params, False)
+    loss3, _, _ = outputs(qf, b, len(circuits), 0, 0)
+    np.testing.assert_allclose(loss3, loss, atol=0)
+    assert info["launches_backward"] > info["launches_forward"] > 0
+    qf.qf_batch_free(b)
+    for p in progs:
+        qf.qf_program_free(p)
+
+
+def test_batch_full_size_sample(orc):
+    """The 4096-circuit workload (d 2..5, n 4..10, L 2..6) in complex64: a
+    sample of circuits against the same circuit run alone."""
+    qf = gpu_lib()
+    circuits, params = W.batch_circuits(count=4096)
+    w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
+    b, progs = make_batch(qf, circuits, params, "c64", w0)
+    qf.qf_batch_run(b, params, True)
+    nlocal = sum(len(qf.qf_batch_circuit_params(b, i)[0]) for i in range(len(circuits)))
+    loss, gl, gs = outputs(qf, b, len(circuits), nlocal, len(params))
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(circuits), 16, replace=False):
+        c = circuits[i]
+        slots, off = qf.qf_batch_circuit_params(b, int(i))
+        psi = qf.State(c.d, c.n, "c64")
+        psi.set_basis(0)
+        lam = qf.State(c.d, c.n, "c64")
+        l1, g1 = qf.qf_program_gradient(progs[i], psi.handle, lam.handle, params, w0(c))
+        psi.free()
+        lam.free()
+        assert abs(loss[i] - l1) <= 2e-6
+        assert np.abs(gl[off:off + len(slots)] - g1[slots]).max() <= 2e-5
+    assert np.isfinite(gs).all()
+    qf.qf_batch_free(b)
+    for p in progs:
+        qf.qf_program_free(p)
