@@ -123,7 +123,7 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_tile.cu", "qf_internal.cuh"):
+    for f in ("k_tile.cu", "tile_device.cuh", "qf_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2409_17716_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -329,6 +329,11 @@ def main():
         qf.qf_program_free(p)
     for st in states:
         st.free()
+    if extras:
+        torch.cuda.empty_cache()
+        line["adjoint"] = adjoint_bench(qf, W, torch, hbm_peak)
+        torch.cuda.empty_cache()
+        line["batched"] = batch_bench(qf, W, torch)
     if extras and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -417,6 +422,111 @@ def per_gate_sweep(qf, W, torch, hbm_peak):
                      "median_frac_wide": (statistics.median(wide) / hbm_peak) if wide else None}
     st.free()
     return out
+
+
+def adjoint_bench(qf, W, torch, hbm_peak):
+    """Full gradient (forward + adjoint) of the variational ansatz vs the
+    forward + central-difference path on the same GPU (2P + 1 forwards)."""
+    out = {}
+    cases = [("d3_n14_L10", 3, 14, 10, ("c64", "c128")), ("d3_n20_L4", 3, 20, 4, ("c64",))]
+    for name, d, n, L, dtypes in cases:
+        ops, P = W.variational_ansatz(d, n, L, entangler="ring" if n == 14 else "chain")
+        theta = W.normal_angles(P, seed=n)
+        w = [1.0] * n
+        for dtype in dtypes:
+            p = qf.program_from_ops(d, n, ops)
+            psi, lam = qf.State(d, n, dtype), qf.State(d, n, dtype)
+            loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+            grad = torch.zeros(P, dtype=torch.float64, device="cuda")
+            ev = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+
+            def fwd():
+                psi.set_basis(0)
+                qf.qf_program_run(p, psi.handle, theta)
+                qf.qf_expect_device(psi.handle, ev.data_ptr(), qf.QF_OBS_NUMBER_ALL)
+
+            def full_grad():
+                psi.set_basis(0)
+                qf.qf_program_run(p, psi.handle, theta)
+                qf.qf_program_adjoint(p, psi.handle, lam.handle, theta, w, loss.data_ptr(), grad.data_ptr())
+
+            reps = 2 if n >= 20 else 5
+            fwd()
+            full_grad()
+            t_f = _time_ms(torch, fwd, reps=reps)
+            fwd_passes = qf.qf_program_last_passes(p)
+            full_grad()
+            adj_passes = qf.qf_program_last_passes(p)
+            t_g = _time_ms(torch, full_grad, reps=reps)
+            N = d ** n
+            b = 8 if dtype == "c64" else 16
+            # algorithmic bytes: forward passes (2Nb each), lambda = O psi (2Nb),
+            # reverse passes over psi and lambda (4Nb each)
+            by = fwd_passes * 2 * N * b + 2 * N * b + adj_passes * 4 * N * b
+            fd_ms = (2 * P + 1) * t_f
+            out[name + "_" + dtype] = {
+                "params": P, "gates": len(ops), "gradient_ms": t_g, "gradients_per_s": P / (t_g / 1e3),
+                "forward_ms": t_f, "fd_gradient_ms": fd_ms, "speedup_vs_fd": fd_ms / t_g,
+                "passes_forward": fwd_passes, "passes_adjoint": adj_passes,
+                "hbm_gbs": by / (t_g / 1e3) / 1e9, "hbm_frac": by / (t_g / 1e3) / 1e9 / hbm_peak,
+                "note": "fd = (2P+1) forward runs of the same fused program on this GPU"}
+            qf.qf_program_free(p)
+            psi.free()
+            lam.free()
+            del ev, grad, loss
+            torch.cuda.empty_cache()
+    return out
+
+
+def batch_bench(qf, W, torch):
+    """4096 circuits (d 2..5, n 4..10, L 2..6), forward + adjoint in one graph
+    replay, vs per-circuit forward + central differences on the same GPU
+    (sampled over 64 circuits and extrapolated)."""
+    import numpy as np
+    circuits, params = W.batch_circuits(count=4096)
+    t0 = time.perf_counter()
+    b = qf.qf_batch_create(qf.QF_C64)
+    progs = []
+    for c in circuits:
+        p = qf.program_from_ops(c.d, c.n, c.ops)
+        qf.qf_batch_add(b, p, [1.0] + [0.0] * (c.n - 1))
+        progs.append(p)
+    qf.qf_batch_build(b, len(params))
+    build_s = time.perf_counter() - t0
+    info = qf.qf_batch_info(b)
+    qf.qf_batch_run(b, params, True)
+    qf.qf_batch_run(b, params, True)
+    t_fb = _time_ms(torch, lambda: qf.qf_batch_run(b, params, True), reps=3)
+    t_f = _time_ms(torch, lambda: qf.qf_batch_run(b, params, False), reps=3)
+    # per-circuit forward + FD baseline on a sample
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(circuits), 64, replace=False)
+    fd_ms = 0.0
+    ev = torch.zeros(16, dtype=torch.float64, device="cuda")
+    for i in sample:
+        c = circuits[i]
+        st = qf.State(c.d, c.n, "c64")
+        P_c = len(qf.qf_batch_circuit_params(b, int(i))[0])
+
+        def fwd():
+            st.set_basis(0)
+            qf.qf_program_run(progs[i], st.handle, params)
+            qf.qf_expect_device(st.handle, ev.data_ptr(), qf.QF_OBS_NUMBER_ALL)
+
+        fwd()
+        fd_ms += (2 * P_c + 1) * _time_ms(torch, fwd, reps=3)
+        st.free()
+    fd_total_ms = fd_ms * len(circuits) / len(sample)
+    qf.qf_batch_free(b)
+    for p in progs:
+        qf.qf_program_free(p)
+    return {"circuits": info["circuits"], "amplitudes": info["amplitudes"],
+            "forward_backward_ms": t_fb, "forward_ms": t_f, "samples_per_s": info["circuits"] / (t_fb / 1e3),
+            "gradients_per_s": info["grad_local_len"] / (t_fb / 1e3),
+            "forward_amplitude_updates_per_s": info["gate_amplitudes"] / (t_f / 1e3),
+            "launches_forward_backward": info["launches_backward"], "build_s": build_s,
+            "fd_per_circuit_ms_extrapolated": fd_total_ms, "speedup_vs_per_circuit_fd": fd_total_ms / t_fb,
+            "note": "fd baseline: per-circuit fused forward + <N_q> on this GPU, (2P_c+1) runs, 64-circuit sample"}
 
 
 def e2e_throughput(qf, W, torch, sizes, progs, args):
