@@ -17,7 +17,7 @@
 //                    term, then U^+ is applied to both tiles
 //   k_grad_gather    per parameter slot, sums its terms over passes and CTAs
 //                    in a fixed order (deterministic)
-#include "tile_device.cuh"
+#include "stage_device.cuh"
 
 namespace qf {
 
@@ -192,6 +192,8 @@ struct AdjArgs {
     int nmat;
     const TOp *ops;
     const cplx<R> *mats;
+    const TStage *stages;   // register stages (nstages > 0), else one op per shared-memory sweep
+    int nstages;
     double *rows;      // gradient rows: gridDim.x rows of ncols doubles
     int ncols;
 };
@@ -236,12 +238,14 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nA = T / g.SEG;
 
-    // layout: psi tile | lambda tile | pool | ops | pad 16 | gacc | offA | base
+    // layout: psi tile | lambda tile | pool | ops | stages | pad 16 | gacc | offA | base
     C *tp = reinterpret_cast<C *>(smem);
     C *tl = tp + T;
     C *mats = tl + T;
     TOp *ops = reinterpret_cast<TOp *>(mats + A.nmat);
-    size_t off = (size_t)2 * T * sizeof(C) + (size_t)A.nmat * sizeof(C) + (size_t)A.nops * sizeof(TOp);
+    TStage *stages = reinterpret_cast<TStage *>(ops + A.nops);
+    size_t off = (size_t)2 * T * sizeof(C) + (size_t)A.nmat * sizeof(C) + (size_t)A.nops * sizeof(TOp) +
+                 (size_t)A.nstages * sizeof(TStage);
     off = (off + 15) & ~(size_t)15;
     double *gacc = reinterpret_cast<double *>(smem + off);
     long long *offA = reinterpret_cast<long long *>(gacc + (size_t)A.nops * kAdjWarps);
@@ -254,7 +258,16 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
         const int words = A.nops * (int)(sizeof(TOp) / sizeof(int));
         for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
     }
+    if (A.nstages > 0) {
+        const int *src = reinterpret_cast<const int *>(A.stages);
+        int *dst = reinterpret_cast<int *>(stages);
+        const int words = A.nstages * (int)(sizeof(TStage) / sizeof(int));
+        for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
+    }
     for (int i = tid; i < A.nops * kAdjWarps; i += kTileBlock) gacc[i] = 0.0;
+    R gsum[kMaxGrad];   // register-stage gradient accumulators, by gradient column
+#pragma unroll
+    for (int c = 0; c < kMaxGrad; ++c) gsum[c] = 0;
     for (int a = tid; a < nA; a += kTileBlock) {
         long long o = 0;
         int rem = a;
@@ -278,6 +291,22 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
         }
         cp_async_wait_all();
         __syncthreads();
+        if constexpr (StageK<R, D, true>::K > 0) {
+            if (A.nstages > 0) {
+                for (int si = 0; si < A.nstages; ++si) {
+                    const TStage &st = stages[si];
+                    if (!st.legacy) {
+                        stage_run<R, D, StageK<R, D, true>::K, true>(st, ops, mats, tp, tl, T, gsum);
+                    } else {
+                        // SWAP / custom gates: no angle
+                        tile_apply<R, D>(ops[st.first], tp, mats, T, g.nt, d);
+                        tile_apply<R, D>(ops[st.first], tl, mats, T, g.nt, d);
+                    }
+                    __syncthreads();
+                }
+                goto store;
+            }
+        }
         for (int o = 0; o < A.nops; ++o) {
             const TOp &op = ops[o];
             const C *M = mats + op.mat;
@@ -302,7 +331,9 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
             tile_apply<R, D>(op, tp, mats, T, g.nt, d);
             tile_apply<R, D>(op, tl, mats, T, g.nt, d);
             __syncthreads();
+            (void)M;
         }
+    store:
         for (int e = tid; e < T; e += kTileBlock) {
             int a = (int)g.divSEG.div((uint32_t)e);
             int lo = e - a * g.SEG;
@@ -312,6 +343,25 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
         }
         if (tid == 0 && t + gridDim.x < g.ntiles) sbase[0] = tile_base(g, t + gridDim.x);
         __syncthreads();
+    }
+    // register-stage accumulators: reduce per column into gacc[col * warps + warp]
+    if (A.nstages > 0 && StageK<R, D, true>::K > 0) {
+        __syncthreads();
+        for (int i = tid; i < A.nops * kAdjWarps; i += kTileBlock) gacc[i] = 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kMaxGrad; ++c) {
+            if (c >= A.ncols) break;
+            const double v = warp_sum_d((double)gsum[c]);
+            if (lane == 0) gacc[c * kAdjWarps + wid] = v;
+        }
+        __syncthreads();
+        for (int c = tid; c < A.ncols; c += kTileBlock) {
+            double s2 = 0.0;
+            for (int w = 0; w < kAdjWarps; ++w) s2 += gacc[c * kAdjWarps + w];
+            A.rows[(long long)blockIdx.x * A.ncols + c] = 2.0 * s2;
+        }
+        return;
     }
     // this CTA's gradient row
     for (int o = tid; o < A.nops; o += kTileBlock) {
@@ -324,8 +374,9 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
 }
 
 template <typename R>
-size_t adj_smem_bytes(const TileGeom &g, int nops, int nmat) {
-    size_t b = (size_t)2 * g.T * sizeof(cplx<R>) + (size_t)nmat * sizeof(cplx<R>) + (size_t)nops * sizeof(TOp);
+size_t adj_smem_bytes(const TileGeom &g, int nops, int nmat, int nstages) {
+    size_t b = (size_t)2 * g.T * sizeof(cplx<R>) + (size_t)nmat * sizeof(cplx<R>) + (size_t)nops * sizeof(TOp) +
+               (size_t)nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
     b += (size_t)nops * kAdjWarps * sizeof(double);
     b += (size_t)(g.T / g.SEG) * sizeof(long long) + 16;
@@ -352,8 +403,8 @@ static cudaError_t adj_grid_d(int num_sms, const TileGeom &g, size_t smem, int *
 
 // Grid the reverse pass will use (the host sizes gradient rows with it).
 template <typename R>
-cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, int *grid) {
-    size_t smem = adj_smem_bytes<R>(g, nops, nmat);
+cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, int nstages, int *grid) {
+    size_t smem = adj_smem_bytes<R>(g, nops, nmat, nstages);
     switch (d) {
 #define QF_CASE(DD) case DD: return adj_grid_d<R, DD>(num_sms, g, smem, grid);
         QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
@@ -364,7 +415,8 @@ cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, 
 
 template <typename R>
 cudaError_t launch_tile_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, int d, const TileGeom &g, int nops,
-                            const TOp *ops_dev, const cplx<R> *mat_dev, int nmat, double *rows, int ncols, int grid) {
+                            const TOp *ops_dev, const cplx<R> *mat_dev, int nmat, const TStage *stages_dev,
+                            int nstages, double *rows, int ncols, int grid) {
     AdjArgs<R> A;
     A.psi = psi;
     A.lam = lam;
@@ -375,7 +427,9 @@ cudaError_t launch_tile_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, int d, 
     A.mats = mat_dev;
     A.rows = rows;
     A.ncols = ncols;
-    size_t smem = adj_smem_bytes<R>(g, nops, nmat);
+    A.stages = stages_dev;
+    A.nstages = stages_dev ? nstages : 0;
+    size_t smem = adj_smem_bytes<R>(g, nops, nmat, A.nstages);
     switch (d) {
 #define QF_CASE(DD) case DD: k_tile_adj<R, DD><<<grid, kTileBlock, smem, L.stream>>>(A, d); break;
         QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
@@ -418,11 +472,13 @@ template cudaError_t launch_number_obs<float>(const Launch &, const cplx<float> 
                                               const double *, double *, double *);
 template cudaError_t launch_number_obs<double>(const Launch &, const cplx<double> *, cplx<double> *, int, int,
                                                const double *, double *, double *);
-template cudaError_t adj_grid<float>(int, int, const TileGeom &, int, int, int *);
-template cudaError_t adj_grid<double>(int, int, const TileGeom &, int, int, int *);
+template cudaError_t adj_grid<float>(int, int, const TileGeom &, int, int, int, int *);
+template cudaError_t adj_grid<double>(int, int, const TileGeom &, int, int, int, int *);
 template cudaError_t launch_tile_adj<float>(const Launch &, cplx<float> *, cplx<float> *, int, const TileGeom &, int,
-                                            const TOp *, const cplx<float> *, int, double *, int, int);
+                                            const TOp *, const cplx<float> *, int, const TStage *, int, double *, int,
+                                            int);
 template cudaError_t launch_tile_adj<double>(const Launch &, cplx<double> *, cplx<double> *, int, const TileGeom &, int,
-                                             const TOp *, const cplx<double> *, int, double *, int, int);
+                                             const TOp *, const cplx<double> *, int, const TStage *, int, double *, int,
+                                             int);
 
 }  // namespace qf

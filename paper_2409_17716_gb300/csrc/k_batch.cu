@@ -12,7 +12,7 @@
 // sequence captured once in a CUDA graph serves every parameter update.  The
 // adjoint variant carries psi and lambda tiles and writes one gradient row per
 // work item (the per-gate terms 2 Im <lambda|G|psi> of its tiles).
-#include "tile_device.cuh"
+#include "stage_device.cuh"
 
 namespace qf {
 
@@ -24,6 +24,7 @@ struct BPass {
     int ncols;                    // adjoint gradient columns
     int chunks;                   // work items of this pass
     long long rows_base;          // adjoint gradient rows (chunks rows of ncols)
+    int stages_off, nstages;      // register stages (nstages = 0: one op per shared-memory sweep)
 };
 
 template <typename R>
@@ -34,10 +35,11 @@ struct BatchArgs {
     int npasses;
     const TOp *ops;
     const cplx<R> *pool;
+    const TStage *stages;
     const double *params;
     double *rows;
     int chunk_tiles;
-    int max_T, max_nmat, max_nops, max_nA;
+    int max_T, max_nmat, max_nops, max_nA, max_nstages;
 };
 
 constexpr int kBatchWarps = kTileBlock / 32;
@@ -124,8 +126,9 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
     C *tl = tp + A.max_T;                              // adjoint only
     C *mats = tl + (ADJ ? A.max_T : 0);
     TOp *ops = reinterpret_cast<TOp *>(mats + A.max_nmat);
+    TStage *stages = reinterpret_cast<TStage *>(ops + A.max_nops);
     size_t off = (size_t)(ADJ ? 2 : 1) * A.max_T * sizeof(C) + (size_t)A.max_nmat * sizeof(C) +
-                 (size_t)A.max_nops * sizeof(TOp);
+                 (size_t)A.max_nops * sizeof(TOp) + (size_t)A.max_nstages * sizeof(TStage);
     off = (off + 15) & ~(size_t)15;
     double *gacc = reinterpret_cast<double *>(smem + off);
     long long *offA = reinterpret_cast<long long *>(gacc + (ADJ ? (size_t)A.max_nops * kBatchWarps : 0));
@@ -153,6 +156,10 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
             int *dst = reinterpret_cast<int *>(ops);
             const int words = P.nops * (int)(sizeof(TOp) / sizeof(int));
             for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
+            const int *ssrc = reinterpret_cast<const int *>(A.stages + P.stages_off);
+            int *sdst = reinterpret_cast<int *>(stages);
+            const int swords = P.nstages * (int)(sizeof(TStage) / sizeof(int));
+            for (int i = tid; i < swords; i += kTileBlock) sdst[i] = ssrc[i];
             for (int a = tid; a < nA; a += kTileBlock) {
                 long long o = 0;
                 int rem = a;
@@ -170,6 +177,11 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
         }
         if (ADJ)
             for (int i = tid; i < P.nops * kBatchWarps; i += kTileBlock) gacc[i] = 0.0;
+        constexpr int KS = StageK<R, D, ADJ>::K;
+        R gsum[ADJ ? kMaxGrad : 1];
+#pragma unroll
+        for (int c = 0; c < (ADJ ? kMaxGrad : 1); ++c) gsum[c] = 0;
+        const bool staged = KS > 0 && P.nstages > 0;
         const long long chunk = item - A.prefix[k];
         const long long t0 = chunk * A.chunk_tiles;
         long long t1 = t0 + A.chunk_tiles;
@@ -189,7 +201,21 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
             }
             cp_async_wait_all();
             __syncthreads();
-            for (int o = 0; o < P.nops; ++o) {
+            if constexpr (KS > 0) {
+                if (staged) {
+                    for (int si = 0; si < P.nstages; ++si) {
+                        const TStage &st = stages[si];
+                        if (!st.legacy) {
+                            stage_run<R, D, KS, ADJ>(st, ops, mats, tp, tl, T, gsum);
+                        } else {
+                            tile_apply<R, D>(ops[st.first], tp, mats, T, g.nt, d);
+                            if (ADJ) tile_apply<R, D>(ops[st.first], tl, mats, T, g.nt, d);
+                        }
+                        __syncthreads();
+                    }
+                }
+            }
+            for (int o = 0; o < (staged ? 0 : P.nops); ++o) {
                 const TOp &op = ops[o];
                 if (ADJ && op.gcol >= 0) {
                     const C *G = mats + op.gmat;
@@ -221,12 +247,28 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
             __syncthreads();
         }
         if (ADJ) {
-            for (int o = tid; o < P.nops; o += kTileBlock) {
-                const TOp &op = ops[o];
-                if (op.gcol < 0) continue;
-                double s = 0.0;
-                for (int w = 0; w < kBatchWarps; ++w) s += gacc[o * kBatchWarps + w];
-                A.rows[P.rows_base + chunk * P.ncols + op.gcol] = 2.0 * s;
+            if (staged) {
+                // register accumulators -> gacc[col * warps + warp]
+#pragma unroll
+                for (int c = 0; c < (ADJ ? kMaxGrad : 1); ++c) {
+                    if (c >= P.ncols) break;
+                    const double v = warp_sum_b((double)gsum[c]);
+                    if (lane == 0) gacc[c * kBatchWarps + wid] = v;
+                }
+                __syncthreads();
+                for (int c = tid; c < P.ncols; c += kTileBlock) {
+                    double s = 0.0;
+                    for (int w = 0; w < kBatchWarps; ++w) s += gacc[c * kBatchWarps + w];
+                    A.rows[P.rows_base + chunk * P.ncols + c] = 2.0 * s;
+                }
+            } else {
+                for (int o = tid; o < P.nops; o += kTileBlock) {
+                    const TOp &op = ops[o];
+                    if (op.gcol < 0) continue;
+                    double s = 0.0;
+                    for (int w = 0; w < kBatchWarps; ++w) s += gacc[o * kBatchWarps + w];
+                    A.rows[P.rows_base + chunk * P.ncols + op.gcol] = 2.0 * s;
+                }
             }
             __syncthreads();
         }
@@ -234,9 +276,9 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
 }
 
 template <typename R>
-size_t batch_smem_bytes(bool adj, int max_T, int max_nmat, int max_nops, int max_nA) {
+size_t batch_smem_bytes(bool adj, int max_T, int max_nmat, int max_nops, int max_nA, int max_nstages) {
     size_t b = (size_t)(adj ? 2 : 1) * max_T * sizeof(cplx<R>) + (size_t)max_nmat * sizeof(cplx<R>) +
-               (size_t)max_nops * sizeof(TOp);
+               (size_t)max_nops * sizeof(TOp) + (size_t)max_nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
     if (adj) b += (size_t)max_nops * kBatchWarps * sizeof(double);
     b += (size_t)max_nA * sizeof(long long) + 16;
@@ -267,8 +309,8 @@ cudaError_t batch_prepare(int d, bool adj, size_t smem, int *per_sm) {
 template <typename R>
 cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t smem, cplx<R> *states, const BPass *passes,
                          const long long *prefix, int npasses, const TOp *ops, const cplx<R> *pool,
-                         const double *params, double *rows, int chunk_tiles, int max_T, int max_nmat, int max_nops,
-                         int max_nA) {
+                         const TStage *stages, const double *params, double *rows, int chunk_tiles, int max_T,
+                         int max_nmat, int max_nops, int max_nA, int max_nstages) {
     BatchArgs<R> A;
     A.states = states;
     A.passes = passes;
@@ -283,6 +325,8 @@ cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t 
     A.max_nmat = max_nmat;
     A.max_nops = max_nops;
     A.max_nA = max_nA;
+    A.stages = stages;
+    A.max_nstages = max_nstages;
     switch (d) {
 #define QF_CASE(DD)                                                                            \
     case DD:                                                                                   \
@@ -391,14 +435,14 @@ size_t bobs_bytes() { return sizeof(BObs); }
 
 template cudaError_t batch_prepare<float>(int, bool, size_t, int *);
 template cudaError_t batch_prepare<double>(int, bool, size_t, int *);
-template size_t batch_smem_bytes<float>(bool, int, int, int, int);
-template size_t batch_smem_bytes<double>(bool, int, int, int, int);
+template size_t batch_smem_bytes<float>(bool, int, int, int, int, int);
+template size_t batch_smem_bytes<double>(bool, int, int, int, int, int);
 template cudaError_t launch_batch<float>(cudaStream_t, int, bool, int, size_t, cplx<float> *, const BPass *,
-                                         const long long *, int, const TOp *, const cplx<float> *, const double *,
-                                         double *, int, int, int, int, int);
+                                         const long long *, int, const TOp *, const cplx<float> *, const TStage *,
+                                         const double *, double *, int, int, int, int, int, int);
 template cudaError_t launch_batch<double>(cudaStream_t, int, bool, int, size_t, cplx<double> *, const BPass *,
-                                          const long long *, int, const TOp *, const cplx<double> *, const double *,
-                                          double *, int, int, int, int, int);
+                                          const long long *, int, const TOp *, const cplx<double> *, const TStage *,
+                                          const double *, double *, int, int, int, int, int, int);
 template cudaError_t launch_batch_init<float>(cudaStream_t, int, cplx<float> *, long long, const long long *, int);
 template cudaError_t launch_batch_init<double>(cudaStream_t, int, cplx<double> *, long long, const long long *, int);
 template cudaError_t launch_batch_obs<float>(cudaStream_t, int, cplx<float> *, const BObs *, const long long *, int,

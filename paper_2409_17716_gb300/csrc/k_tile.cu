@@ -11,7 +11,7 @@
 // run), applies the pass's gate list with a barrier between gates, and writes
 // the tile back: each pass costs one read and one write of the state in HBM
 // however many gates it holds.  CTAs are persistent over tiles.
-#include "tile_device.cuh"
+#include "stage_device.cuh"
 
 namespace qf {
 
@@ -23,6 +23,8 @@ struct TileArgs {
     int nmat;
     const TOp *ops_g;          // device op list, or nullptr -> op_i
     const cplx<R> *mat_g;      // device matrix pool, or nullptr -> mat_i
+    const TStage *stages_g;    // register stages, or nullptr: every op through shared memory
+    int nstages;
     TOp op_i;
     cplx<R> mat_i[kInlineMat];
 };
@@ -37,11 +39,13 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
     const int tid = threadIdx.x;
     const int nA = T / g.SEG;   // d^kA runs per tile
 
-    // layout (must match tile_smem_bytes): tile | pool | ops | pad to 16 | offA | base
+    // layout (must match tile_smem_bytes): tile | pool | ops | stages | pad to 16 | offA | base
     C *tile = reinterpret_cast<C *>(smem);
     C *mats = tile + T;
     TOp *ops = reinterpret_cast<TOp *>(mats + A.nmat);
-    size_t off = (size_t)T * sizeof(C) + (size_t)A.nmat * sizeof(C) + (size_t)A.nops * sizeof(TOp);
+    TStage *stages = reinterpret_cast<TStage *>(ops + A.nops);
+    size_t off = (size_t)T * sizeof(C) + (size_t)A.nmat * sizeof(C) + (size_t)A.nops * sizeof(TOp) +
+                 (size_t)A.nstages * sizeof(TStage);
     off = (off + 15) & ~(size_t)15;
     long long *offA = reinterpret_cast<long long *>(smem + off);
     long long *sbase = offA + nA;
@@ -56,6 +60,12 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
         for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
     } else if (tid == 0) {
         ops[0] = A.op_i;
+    }
+    if (A.nstages > 0) {
+        const int *src = reinterpret_cast<const int *>(A.stages_g);
+        int *dst = reinterpret_cast<int *>(stages);
+        const int words = A.nstages * (int)(sizeof(TStage) / sizeof(int));
+        for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
     }
     for (int a = tid; a < nA; a += kTileBlock) {
         long long off = 0;
@@ -79,9 +89,23 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
         }
         cp_async_wait_all();
         __syncthreads();
-        for (int o = 0; o < A.nops; ++o) {
-            tile_apply<R, D>(ops[o], tile, mats, T, g.nt, d);
-            __syncthreads();
+        if (A.nstages > 0) {
+            for (int si = 0; si < A.nstages; ++si) {
+                const TStage &st = stages[si];
+                if constexpr (StageK<R, D, false>::K > 0) {
+                    if (!st.legacy)
+                        stage_run<R, D, StageK<R, D, false>::K, false>(st, ops, mats, tile, nullptr, T, nullptr);
+                    else tile_apply<R, D>(ops[st.first], tile, mats, T, g.nt, d);
+                } else {
+                    tile_apply<R, D>(ops[st.first], tile, mats, T, g.nt, d);
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int o = 0; o < A.nops; ++o) {
+                tile_apply<R, D>(ops[o], tile, mats, T, g.nt, d);
+                __syncthreads();
+            }
         }
         C *dst = A.psi + base;
         for (int e = tid; e < T; e += kTileBlock) {
@@ -95,8 +119,9 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
 }
 
 template <typename R>
-size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat) {
-    size_t b = (size_t)g.T * sizeof(cplx<R>) + (size_t)nmat * sizeof(cplx<R>) + (size_t)nops * sizeof(TOp);
+size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat, int nstages) {
+    size_t b = (size_t)g.T * sizeof(cplx<R>) + (size_t)nmat * sizeof(cplx<R>) + (size_t)nops * sizeof(TOp) +
+               (size_t)nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
     b += (size_t)(g.T / g.SEG) * sizeof(long long) + 16;
     return b;
@@ -125,7 +150,8 @@ static cudaError_t launch_tile_d(const Launch &L, const TileArgs<R> &A, int d, s
 // `mat_i` is used.
 template <typename R>
 cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g, int nops, const TOp *ops_dev,
-                        const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i) {
+                        const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i,
+                        const TStage *stages_dev, int nstages) {
     TileArgs<R> A;
     A.psi = psi;
     A.g = g;
@@ -133,12 +159,14 @@ cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g,
     A.nmat = nmat;
     A.ops_g = ops_dev;
     A.mat_g = mat_dev;
+    A.stages_g = stages_dev;
+    A.nstages = stages_dev ? nstages : 0;
     if (!ops_dev) {
         if (nops != 1 || nmat > kInlineMat) return cudaErrorInvalidValue;
         A.op_i = *op_i;
         for (int i = 0; i < nmat; ++i) A.mat_i[i] = mat_i[i];
     }
-    size_t smem = tile_smem_bytes<R>(g, nops, nmat);
+    size_t smem = tile_smem_bytes<R>(g, nops, nmat, A.nstages);
     switch (d) {
 #define QF_CASE(DD) case DD: return launch_tile_d<R, DD>(L, A, d, smem);
         QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
@@ -147,11 +175,12 @@ cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g,
     }
 }
 
-template size_t tile_smem_bytes<float>(const TileGeom &, int, int);
-template size_t tile_smem_bytes<double>(const TileGeom &, int, int);
+template size_t tile_smem_bytes<float>(const TileGeom &, int, int, int);
+template size_t tile_smem_bytes<double>(const TileGeom &, int, int, int);
 template cudaError_t launch_tile<float>(const Launch &, cplx<float> *, int, const TileGeom &, int, const TOp *,
-                                        const cplx<float> *, int, const TOp *, const cplx<float> *);
+                                        const cplx<float> *, int, const TOp *, const cplx<float> *, const TStage *, int);
 template cudaError_t launch_tile<double>(const Launch &, cplx<double> *, int, const TileGeom &, int, const TOp *,
-                                         const cplx<double> *, int, const TOp *, const cplx<double> *);
+                                         const cplx<double> *, int, const TOp *, const cplx<double> *, const TStage *,
+                                         int);
 
 }  // namespace qf

@@ -30,6 +30,7 @@ struct BPassHost {  // mirrors BPass in k_batch.cu
     int ncols;
     int chunks;
     long long rows_base;
+    int stages_off, nstages;
 };
 struct BObsHost {  // mirrors BObs in k_batch.cu
     long long psi_off, lam_off;
@@ -43,13 +44,13 @@ size_t bobs_bytes();
 template <typename R>
 cudaError_t batch_prepare(int d, bool adj, size_t smem, int *per_sm);
 template <typename R>
-size_t batch_smem_bytes(bool adj, int max_T, int max_nmat, int max_nops, int max_nA);
+size_t batch_smem_bytes(bool adj, int max_T, int max_nmat, int max_nops, int max_nA, int max_nstages);
 struct BPass;
 template <typename R>
 cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t smem, cplx<R> *states,
                          const BPass *passes, const long long *prefix, int npasses, const TOp *ops, const cplx<R> *pool,
-                         const double *params, double *rows, int chunk_tiles, int max_T, int max_nmat, int max_nops,
-                         int max_nA);
+                         const TStage *stages, const double *params, double *rows, int chunk_tiles, int max_T,
+                         int max_nmat, int max_nops, int max_nA, int max_nstages);
 struct BObs;
 template <typename R>
 cudaError_t launch_batch_init(cudaStream_t stream, int sms, cplx<R> *states, long long psi_elems, const long long *offs,
@@ -188,7 +189,7 @@ struct LaunchRec {
     bool adj = false;
     int first = 0, count = 0;   // BPass range
     long long prefix_off = 0;   // into the prefix table
-    int max_T = 0, max_nmat = 0, max_nops = 0, max_nA = 0;
+    int max_T = 0, max_nmat = 0, max_nops = 0, max_nA = 0, max_nstages = 0;
     size_t smem = 0;
     int grid = 0;
 };
@@ -244,6 +245,7 @@ static qf_status build_t(qf_batch *b) {
     std::vector<long long> prefix;
     std::vector<TOp> ops;
     std::vector<C> pool;
+    std::vector<TStage> stages;
     std::vector<LaunchRec> fwd, adj;
     long long rows_total = 0;
     // gradient terms: for local index (grad_off + k): list of (rows_base, chunks, ncols, col)
@@ -327,6 +329,18 @@ static qf_status build_t(qf_batch *b) {
         bp.nops = (int)ops.size() - bp.ops_off;
         bp.nmat = (int)pool.size() - bp.mat_off;
         bp.ncols = ncols;
+        {
+            const int K = stage_k(c.d, is_adj, c128);
+            bp.stages_off = (int)stages.size();
+            bp.nstages = 0;
+            if (K > 0) {
+                std::vector<TOp> pops(ops.begin() + bp.ops_off, ops.end());
+                std::vector<TStage> ps = build_stages(pops, pp.geom, c.d, K);
+                std::copy(pops.begin(), pops.end(), ops.begin() + bp.ops_off);
+                stages.insert(stages.end(), ps.begin(), ps.end());
+                bp.nstages = (int)ps.size();
+            }
+        }
         bp.chunks = (int)((pp.geom.ntiles + kChunkTiles - 1) / kChunkTiles);
         bp.rows_base = rows_total;
         if (is_adj) {
@@ -347,6 +361,7 @@ static qf_status build_t(qf_batch *b) {
         L.max_nmat = std::max(L.max_nmat, bp.nmat);
         L.max_nops = std::max(L.max_nops, bp.nops);
         L.max_nA = std::max(L.max_nA, pp.geom.T / pp.geom.SEG);
+        L.max_nstages = std::max(L.max_nstages, bp.nstages);
         prefix.push_back(prefix.back() + bp.chunks);
         passes.push_back(bp);
     };
@@ -427,6 +442,7 @@ static qf_status build_t(qf_batch *b) {
     size_t o_pref = sz;  sz = al16(sz + prefix.size() * sizeof(long long));
     size_t o_ops = sz;   sz = al16(sz + ops.size() * sizeof(TOp));
     size_t o_pool = sz;  sz = al16(sz + pool.size() * sizeof(C));
+    size_t o_stg = sz;   sz = al16(sz + std::max<size_t>(stages.size(), 1) * sizeof(TStage));
     size_t o_obs = sz;   sz = al16(sz + obs.size() * bobs_bytes());
     size_t o_opref = sz; sz = al16(sz + oprefix.size() * sizeof(long long));
     size_t o_w = sz;     sz = al16(sz + wts.size() * sizeof(double));
@@ -445,6 +461,7 @@ static qf_status build_t(qf_batch *b) {
     put(o_pref, prefix.data(), prefix.size() * sizeof(long long));
     put(o_ops, ops.data(), ops.size() * sizeof(TOp));
     put(o_pool, pool.data(), pool.size() * sizeof(C));
+    put(o_stg, stages.data(), stages.size() * sizeof(TStage));
     put(o_obs, obs.data(), obs.size() * sizeof(BObsHost));
     put(o_opref, oprefix.data(), oprefix.size() * sizeof(long long));
     put(o_w, wts.data(), wts.size() * sizeof(double));
@@ -474,7 +491,7 @@ static qf_status build_t(qf_batch *b) {
     std::map<std::pair<int, int>, size_t> group_smem;
     for (auto *list : {&fwd, &adj})
         for (LaunchRec &L : *list) {
-            L.smem = batch_smem_bytes<R>(L.adj, L.max_T, L.max_nmat, L.max_nops, L.max_nA);
+            L.smem = batch_smem_bytes<R>(L.adj, L.max_T, L.max_nmat, L.max_nops, L.max_nA, L.max_nstages);
             size_t &gs = group_smem[{L.d, L.adj ? 1 : 0}];
             gs = std::max(gs, L.smem);
         }
@@ -512,7 +529,8 @@ static qf_status build_t(qf_batch *b) {
                                 reinterpret_cast<const BPass *>(tab + o_pass + (size_t)L.first * sizeof(BPassHost)),
                                 reinterpret_cast<const long long *>(tab + o_pref) + L.prefix_off, L.count,
                                 reinterpret_cast<const TOp *>(tab + o_ops), reinterpret_cast<const C *>(tab + o_pool),
-                                b->d_params, b->d_rows, kChunkTiles, L.max_T, L.max_nmat, L.max_nops, L.max_nA);
+                                reinterpret_cast<const TStage *>(tab + o_stg), b->d_params, b->d_rows, kChunkTiles,
+                                L.max_T, L.max_nmat, L.max_nops, L.max_nA, L.max_nstages);
             ++nl;
         }
         if (e == cudaSuccess) {
@@ -533,8 +551,9 @@ static qf_status build_t(qf_batch *b) {
                                     reinterpret_cast<const BPass *>(tab + o_pass + (size_t)L.first * sizeof(BPassHost)),
                                     reinterpret_cast<const long long *>(tab + o_pref) + L.prefix_off, L.count,
                                     reinterpret_cast<const TOp *>(tab + o_ops),
-                                    reinterpret_cast<const C *>(tab + o_pool), b->d_params, b->d_rows, kChunkTiles,
-                                    L.max_T, L.max_nmat, L.max_nops, L.max_nA);
+                                    reinterpret_cast<const C *>(tab + o_pool),
+                                    reinterpret_cast<const TStage *>(tab + o_stg), b->d_params, b->d_rows, kChunkTiles,
+                                    L.max_T, L.max_nmat, L.max_nops, L.max_nA, L.max_nstages);
                 ++nl;
             }
             if (e == cudaSuccess && goff > 0) {

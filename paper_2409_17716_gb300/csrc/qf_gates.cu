@@ -372,6 +372,7 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
     while (!remaining.empty()) {
         std::vector<bool> inset(n, false), blocked(n, false);
         std::vector<int> members, deferred;
+        int nparam = 0;
         size_t scan = 0;
         for (; scan < remaining.size(); ++scan) {
             const int gi = remaining[scan];
@@ -379,7 +380,9 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
             bool is_blocked = false;
             for (int q : qs) is_blocked |= blocked[q];
             bool take = false;
-            if (!is_blocked && (int)members.size() < op_cap && (fuse || members.empty())) {
+            // adjoint passes keep at most kMaxGrad gradient columns (register accumulators)
+            const bool param_full = for_adjoint && gate_is_param(gates[gi]) && nparam >= kMaxGrad;
+            if (!is_blocked && !param_full && (int)members.size() < op_cap && (fuse || members.empty())) {
                 std::vector<bool> trial = inset;
                 for (int q : qs) trial[q] = true;
                 if (fit_rl(trial, n, nt_max, rl_min) >= 0) {
@@ -389,6 +392,7 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
             }
             if (take) {
                 members.push_back(gi);
+                if (gate_is_param(gates[gi])) ++nparam;
             } else {
                 deferred.push_back(gi);
                 for (int q : qs) blocked[q] = true;
@@ -411,6 +415,80 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
         remaining.swap(deferred);
     }
     return plan;
+}
+
+// Groups a pass's ops (already in tile-local form, in application order)
+// into register stages of up to stage_k(d) local qudits.  An op joins the
+// current stage if the union of the stage's qudits and the qudits the op must
+// hold in registers (its target; none for a diagonal op, which can use a
+// block-constant digit) stays within K.  SWAP and custom k-qudit gates are
+// shared-memory ops of their own.  Leftover slots take diagonal targets and
+// controls of the stage's ops, then the most significant free positions
+// (which keeps consecutive threads on consecutive shared-memory words).
+std::vector<TStage> build_stages(std::vector<TOp> &ops, const TileGeom &g, int d, int K) {
+    std::vector<TStage> st;
+    const int nt = g.nt;
+    // a tile narrower than K runs every op through shared memory (the kernels
+    // treat an empty stage list that way, gradients included)
+    if (K == 0 || nt < K) return st;
+    auto legacy_kind = [](const TOp &o) { return o.kind == OP_SWAP || o.kind == OP_DENSEK; };
+    auto has = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
+    size_t i = 0;
+    while (i < ops.size()) {
+        if (legacy_kind(ops[i])) {
+            TStage t;
+            std::memset(&t, 0, sizeof(t));
+            t.legacy = 1;
+            t.first = (int)i;
+            t.nops = 1;
+            st.push_back(t);
+            ++i;
+            continue;
+        }
+        std::vector<int> Q;
+        size_t j = i;
+        while (j < ops.size() && !legacy_kind(ops[j])) {
+            std::vector<int> nq = Q;
+            if (ops[j].kind != OP_DIAG && !has(nq, ops[j].a)) nq.push_back(ops[j].a);
+            if ((int)nq.size() > K) break;
+            Q.swap(nq);
+            ++j;
+        }
+        for (size_t k = i; k < j && (int)Q.size() < K; ++k)
+            if (ops[k].kind == OP_DIAG && !has(Q, ops[k].a)) Q.push_back(ops[k].a);
+        for (size_t k = i; k < j && (int)Q.size() < K; ++k)
+            if (is_controlled(ops[k]) && !has(Q, ops[k].c)) Q.push_back(ops[k].c);
+        for (int p = 0; p < nt && (int)Q.size() < K; ++p)
+            if (!has(Q, p)) Q.push_back(p);
+        std::sort(Q.begin(), Q.end());
+        TStage t;
+        std::memset(&t, 0, sizeof(t));
+        t.legacy = 0;
+        t.first = (int)i;
+        t.nops = (int)(j - i);
+        std::vector<int> asc;
+        for (int x = 0; x < K; ++x) {
+            t.ls[x] = (int)ipow_ll(d, nt - 1 - Q[x]);
+            asc.push_back(t.ls[x]);
+        }
+        std::sort(asc.begin(), asc.end());
+        for (int x = 0; x < K; ++x) {
+            t.lsa[x] = asc[x];
+            t.fa[x] = FastDiv((uint32_t)asc[x]);
+        }
+        auto slot_of = [&](int pos) {
+            for (int x = 0; x < K; ++x)
+                if (Q[x] == pos) return x;
+            return -1;
+        };
+        for (size_t k = i; k < j; ++k) {
+            ops[k].q[4] = slot_of(ops[k].a);
+            ops[k].q[5] = is_controlled(ops[k]) ? slot_of(ops[k].c) : -1;
+        }
+        st.push_back(t);
+        i = j;
+    }
+    return st;
 }
 
 }  // namespace qf

@@ -16,9 +16,10 @@ template <typename R>
 cudaError_t launch_strided(const Launch &L, cplx<R> *psi, int d, int n, const TOp &op, const cplx<R> *mat, int nmat);
 template <typename R>
 cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g, int nops, const TOp *ops_dev,
-                        const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i);
+                        const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i,
+                        const TStage *stages_dev = nullptr, int nstages = 0);
 template <typename R>
-size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat);
+size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat, int nstages = 0);
 template <typename R>
 cudaError_t launch_basis(const Launch &L, cplx<R> *psi, long long N, long long index);
 template <typename R>
@@ -31,10 +32,11 @@ template <typename R>
 cudaError_t launch_number_obs(const Launch &L, const cplx<R> *psi, cplx<R> *lam, int d, int n, const double *w,
                               double *partials, double *loss_dev);
 template <typename R>
-cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, int *grid);
+cudaError_t adj_grid(int num_sms, int d, const TileGeom &g, int nops, int nmat, int nstages, int *grid);
 template <typename R>
 cudaError_t launch_tile_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, int d, const TileGeom &g, int nops,
-                            const TOp *ops_dev, const cplx<R> *mat_dev, int nmat, double *rows, int ncols, int grid);
+                            const TOp *ops_dev, const cplx<R> *mat_dev, int nmat, const TStage *stages_dev,
+                            int nstages, double *rows, int ncols, int grid);
 cudaError_t launch_grad_gather(const Launch &L, const double *rows, const void *terms, const int *first, int nslots,
                                double *grad);
 size_t gather_term_bytes();
@@ -103,6 +105,9 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
 
 // Tile geometry for the given active qudits and low-qudit count.
 TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);
+// Register stages of K slots over a pass's localized ops (sets the ops'
+// stage slots); K = stage_k(d, adjoint, complex128) of the kernel that runs them.
+std::vector<TStage> build_stages(std::vector<TOp> &ops, const TileGeom &g, int d, int K);
 // Local position of global qudit q in a tile geometry (-1 if not in the tile).
 int local_pos(const TileGeom &g, const std::vector<int> &active, int n, int q);
 // Converts a resolved op on global qudits into tile-local form.

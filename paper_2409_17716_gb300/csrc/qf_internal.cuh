@@ -122,6 +122,32 @@ struct TOp {
 static_assert(sizeof(TOp) % sizeof(int) == 0, "TOp is copied as ints");
 static_assert(alignof(TOp) == 4, "TOp packs into shared memory after the matrix pool");
 
+// A register stage of a tile pass (see stage_device.cuh): ops[first ..
+// first+nops) applied to blocks of d^K amplitudes spanning K local qudits
+// ("slots", strides ls, most significant first).  legacy = 1: the single op
+// ops[first] is applied through shared memory instead.  The slot of an op's
+// target and control within the stage are stored in TOp::q[4] and q[5]
+// (-1: not a slot).
+constexpr int kMaxStageK = 4;
+constexpr int kMaxGrad = 16;   // parametrised ops per adjoint pass (register accumulators)
+
+struct TStage {
+    int legacy;
+    int first, nops;
+    int ls[kMaxStageK];        // local strides of the slots, most significant first
+    int lsa[kMaxStageK];       // the same strides ascending
+    FastDiv fa[kMaxStageK];    // divisors by lsa
+};
+
+// Slots per register stage (0: shared-memory ops only), chosen so the
+// register blocks (psi, and lambda for the adjoint) fit without spilling.
+__host__ __device__ constexpr int stage_k(int d, bool adj, bool c128) {
+    return d == 2   ? (adj ? (c128 ? 2 : 3) : (c128 ? 3 : 4))
+           : d == 3 ? ((adj && c128) ? 1 : 2)
+           : (d == 4 || d == 5) ? ((adj || c128) ? 1 : 2)
+                                : 0;
+}
+
 // Geometry of a tile pass.
 struct TileGeom {
     int nt;                 // local qudits = kA + rL

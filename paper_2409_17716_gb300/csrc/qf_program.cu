@@ -19,6 +19,7 @@ struct qf_program {
     std::vector<HGate> gates;
     int num_params = 0;
     bool fuse = true;
+    bool stages = true;                // register stages in tile passes
     bool plan_valid = false;
     bool plan_c128 = false;
     std::vector<PassPlan> plan;
@@ -230,7 +231,7 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         bool strided;
         ROp rop;
         size_t off = 0;
-        int nops = 0, nmat = 0;
+        int nops = 0, nmat = 0, nstages = 0;
     };
     std::vector<Built> built(p->plan.size());
     std::vector<unsigned char> host;
@@ -251,13 +252,17 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
             for (const cd &z : r.m) pool.push_back(mk<R>((R)z.real(), (R)z.imag()));
             ops.push_back(o);
         }
+        std::vector<TStage> stages = build_stages(ops, pp.geom, d, stage_k(d, false, c128));
         b.nops = (int)ops.size();
         b.nmat = (int)pool.size();
+        b.nstages = (int)stages.size();
         b.off = align16(host.size());
-        size_t need = b.off + align16(pool.size() * sizeof(C)) + ops.size() * sizeof(TOp);
-        host.resize(need);
+        const size_t ops_at = b.off + align16(pool.size() * sizeof(C));
+        const size_t st_at = ops_at + ops.size() * sizeof(TOp);
+        host.resize(st_at + stages.size() * sizeof(TStage));
         std::memcpy(host.data() + b.off, pool.data(), pool.size() * sizeof(C));
-        std::memcpy(host.data() + b.off + align16(pool.size() * sizeof(C)), ops.data(), ops.size() * sizeof(TOp));
+        std::memcpy(host.data() + ops_at, ops.data(), ops.size() * sizeof(TOp));
+        std::memcpy(host.data() + st_at, stages.data(), stages.size() * sizeof(TStage));
     }
     qf_status ust = upload(p, s, host);
     if (ust != QF_OK) return ust;
@@ -300,7 +305,9 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
             const unsigned char *base = reinterpret_cast<const unsigned char *>(p->d_buf) + b.off;
             const C *pool = reinterpret_cast<const C *>(base);
             const TOp *ops = reinterpret_cast<const TOp *>(base + align16(b.nmat * sizeof(C)));
-            e = launch_tile<R>(L, psi, d, pp.geom, b.nops, ops, pool, b.nmat, nullptr, nullptr);
+            const TStage *stg = reinterpret_cast<const TStage *>(ops + b.nops);
+            e = launch_tile<R>(L, psi, d, pp.geom, b.nops, ops, pool, b.nmat, nullptr, nullptr,
+                               p->stages ? stg : nullptr, b.nstages);
         }
         if (e != cudaSuccess) return cuda_error(e, "program pass");
         ++launched;
@@ -333,7 +340,7 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     const int np = (int)plan.size();
     struct Built {
         size_t off = 0;
-        int nops = 0, nmat = 0, ncols = 0, grid = 0;
+        int nops = 0, nmat = 0, ncols = 0, grid = 0, nstages = 0;
         long long rows_base = 0;
     };
     std::vector<Built> built(np);
@@ -364,17 +371,23 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
             }
             ops.push_back(o);
         }
+        std::vector<TStage> stages;
+        if (p->stages && stage_k(d, true, c128) > 0) stages = build_stages(ops, pp.geom, d, stage_k(d, true, c128));
         b.nops = (int)ops.size();
         b.nmat = (int)pool.size();
         b.ncols = ncols;
-        cudaError_t e = adj_grid<R>(psi->num_sms, d, pp.geom, b.nops, b.nmat, &b.grid);
+        b.nstages = (int)stages.size();
+        cudaError_t e = adj_grid<R>(psi->num_sms, d, pp.geom, b.nops, b.nmat, b.nstages, &b.grid);
         if (e != cudaSuccess) return cuda_error(e, "adjoint pass occupancy");
         b.rows_base = rows_total;
         rows_total += (long long)b.grid * ncols;
         b.off = align16(host.size());
-        host.resize(b.off + align16(pool.size() * sizeof(C)) + ops.size() * sizeof(TOp));
+        const size_t ops_at = b.off + align16(pool.size() * sizeof(C));
+        const size_t st_at = ops_at + ops.size() * sizeof(TOp);
+        host.resize(st_at + stages.size() * sizeof(TStage));
         std::memcpy(host.data() + b.off, pool.data(), pool.size() * sizeof(C));
-        std::memcpy(host.data() + b.off + align16(pool.size() * sizeof(C)), ops.data(), ops.size() * sizeof(TOp));
+        std::memcpy(host.data() + ops_at, ops.data(), ops.size() * sizeof(TOp));
+        std::memcpy(host.data() + st_at, stages.data(), stages.size() * sizeof(TStage));
     }
     // gather table
     const size_t tb = gather_term_bytes();
@@ -431,7 +444,9 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
         const Built &b = built[k];
         const C *pool = reinterpret_cast<const C *>(dev + b.off);
         const TOp *ops = reinterpret_cast<const TOp *>(dev + b.off + align16(b.nmat * sizeof(C)));
-        e = launch_tile_adj<R>(L, ps, ls, d, pp.geom, b.nops, ops, pool, b.nmat, p->d_rows + b.rows_base, b.ncols, b.grid);
+        const TStage *stg = b.nstages > 0 ? reinterpret_cast<const TStage *>(ops + b.nops) : nullptr;
+        e = launch_tile_adj<R>(L, ps, ls, d, pp.geom, b.nops, ops, pool, b.nmat, stg, b.nstages, p->d_rows + b.rows_base,
+                               b.ncols, b.grid);
         if (e != cudaSuccess) return cuda_error(e, "adjoint pass");
     }
     e = launch_grad_gather(L, p->d_rows, dev + terms_off, reinterpret_cast<const int *>(dev + first_off), p->num_params,
