@@ -6,10 +6,11 @@
 // op list and matrix pool into shared memory when the item belongs to a new
 // pass, and runs each tile as the single-circuit kernels do (load with
 // cp.async, apply every op, store).  Rotation entries of parametrised gates
-// are computed on the device from the parameter vector when a pass is staged
-// (Appendix B, "Generalized rotation gate": R = exp(-i theta S / 2); the
-// controlled rotation uses R(m theta) for control level m), so a launch
-// sequence captured once in a CUDA graph serves every parameter update.  The
+// are computed on the device from the parameter vector by one kernel at the
+// start of each run (Appendix B, "Generalized rotation gate": R = exp(-i theta
+// S / 2); the controlled rotation uses R(m theta) for control level m), so a
+// launch sequence captured once in a CUDA graph serves every parameter update.
+// The
 // adjoint variant carries psi and lambda tiles and writes one gradient row per
 // work item (the per-gate terms 2 Im <lambda|G|psi> of its tiles).
 #include "stage_device.cuh"
@@ -169,10 +170,6 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
                 }
                 offA[a] = o;
             }
-            __syncthreads();
-            // device-side rotation entries of parametrised ops
-            for (int o = tid; o < P.nops; o += kTileBlock)
-                if (ops[o].pslot >= 0) resolve_param_op<R>(ops[o], A.params, d, mats);
             cur = k;
         }
         if (ADJ)
@@ -343,6 +340,42 @@ cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ rotation entries
+// One record per parametrised op of the batch tables: its entries are written
+// into the pool once per run, before any pass reads them.
+struct BParam {
+    int pool_off;     // absolute pool offset of the op's entries
+    int kind, d, j, k, axis, slot, sign;
+};
+
+template <typename R>
+__global__ void k_batch_resolve(cplx<R> *pool, const BParam *recs, int count, const double *params) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const BParam r = recs[i];
+        TOp op;
+        op.kind = r.kind;
+        op.j = r.j;
+        op.k = r.k;
+        op.paxis = r.axis;
+        op.pslot = r.slot;
+        op.psign = r.sign;
+        op.mat = r.pool_off;
+        resolve_param_op<R>(op, params, r.d, pool);
+    }
+}
+
+template <typename R>
+cudaError_t launch_batch_resolve(cudaStream_t stream, int sms, cplx<R> *pool, const void *recs, int count,
+                                 const double *params) {
+    if (count <= 0) return cudaSuccess;
+    int blocks = (count + 127) / 128;
+    if (blocks > 8 * sms) blocks = 8 * sms;
+    k_batch_resolve<R><<<blocks, 128, 0, stream>>>(pool, reinterpret_cast<const BParam *>(recs), count, params);
+    return cudaGetLastError();
+}
+
+size_t bparam_bytes() { return sizeof(BParam); }
+
 // ------------------------------------------------------------------ batched |0..0>, lambda = O psi, loss
 struct BObs {
     long long psi_off, lam_off;
@@ -443,6 +476,8 @@ template cudaError_t launch_batch<float>(cudaStream_t, int, bool, int, size_t, c
 template cudaError_t launch_batch<double>(cudaStream_t, int, bool, int, size_t, cplx<double> *, const BPass *,
                                           const long long *, int, const TOp *, const cplx<double> *, const TStage *,
                                           const double *, double *, int, int, int, int, int, int);
+template cudaError_t launch_batch_resolve<float>(cudaStream_t, int, cplx<float> *, const void *, int, const double *);
+template cudaError_t launch_batch_resolve<double>(cudaStream_t, int, cplx<double> *, const void *, int, const double *);
 template cudaError_t launch_batch_init<float>(cudaStream_t, int, cplx<float> *, long long, const long long *, int);
 template cudaError_t launch_batch_init<double>(cudaStream_t, int, cplx<double> *, long long, const long long *, int);
 template cudaError_t launch_batch_obs<float>(cudaStream_t, int, cplx<float> *, const BObs *, const long long *, int,

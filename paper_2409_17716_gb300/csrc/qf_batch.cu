@@ -6,7 +6,8 @@
 // structure share one plan.  For each qudit dimension d present, launch k of
 // the forward runs pass k of every circuit of that d, and launch k of the
 // adjoint runs each circuit's passes in reverse.  The whole sequence --
-// |0...0> initialisation, forward passes, lambda = O psi with
+// the rotation entries of every parametrised op, |0...0> initialisation,
+// forward passes, lambda = O psi with
 // the per-circuit loss, reverse passes and the gradient gathers -- is captured
 // once into a CUDA graph and replayed by qf_batch_run after the parameter
 // upload.  Rotation entries are
@@ -51,6 +52,14 @@ cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t 
                          const BPass *passes, const long long *prefix, int npasses, const TOp *ops, const cplx<R> *pool,
                          const TStage *stages, const double *params, double *rows, int chunk_tiles, int max_T,
                          int max_nmat, int max_nops, int max_nA, int max_nstages);
+struct BParamHost {  // mirrors BParam in k_batch.cu
+    int pool_off;
+    int kind, d, j, k, axis, slot, sign;
+};
+size_t bparam_bytes();
+template <typename R>
+cudaError_t launch_batch_resolve(cudaStream_t stream, int sms, cplx<R> *pool, const void *recs, int count,
+                                 const double *params);
 struct BObs;
 template <typename R>
 cudaError_t launch_batch_init(cudaStream_t stream, int sms, cplx<R> *states, long long psi_elems, const long long *offs,
@@ -246,6 +255,7 @@ static qf_status build_t(qf_batch *b) {
     std::vector<TOp> ops;
     std::vector<C> pool;
     std::vector<TStage> stages;
+    std::vector<BParamHost> precs;   // parametrised ops whose entries the device writes
     std::vector<LaunchRec> fwd, adj;
     long long rows_total = 0;
     // gradient terms: for local index (grad_off + k): list of (rows_base, chunks, ncols, col)
@@ -315,6 +325,7 @@ static qf_status build_t(qf_batch *b) {
                 o.paxis = g0.axis;
                 o.psign = is_adj ? -1 : 1;
                 const int ne = param_entries(o, c.d);
+                precs.push_back({(int)pool.size(), o.kind, c.d, o.j, o.k, o.paxis, o.pslot, o.psign});
                 for (int i = 0; i < ne; ++i) pool.push_back(mk<R>(0, 0));   // written on the device
             } else {
                 for (const cd &z : m) pool.push_back(mk<R>((R)z.real(), (R)z.imag()));
@@ -443,6 +454,7 @@ static qf_status build_t(qf_batch *b) {
     size_t o_ops = sz;   sz = al16(sz + ops.size() * sizeof(TOp));
     size_t o_pool = sz;  sz = al16(sz + pool.size() * sizeof(C));
     size_t o_stg = sz;   sz = al16(sz + std::max<size_t>(stages.size(), 1) * sizeof(TStage));
+    size_t o_prec = sz;  sz = al16(sz + std::max<size_t>(precs.size(), 1) * sizeof(BParamHost));
     size_t o_obs = sz;   sz = al16(sz + obs.size() * bobs_bytes());
     size_t o_opref = sz; sz = al16(sz + oprefix.size() * sizeof(long long));
     size_t o_w = sz;     sz = al16(sz + wts.size() * sizeof(double));
@@ -451,7 +463,8 @@ static qf_status build_t(qf_batch *b) {
     size_t o_fg = sz;    sz = al16(sz + f_local.size() * sizeof(int));
     size_t o_fs = sz;    sz = al16(sz + f_sum.size() * sizeof(int));
     size_t o_one = sz;   sz = al16(sz + one_offs.size() * sizeof(long long));
-    if (bpass_bytes() != sizeof(BPassHost) || bobs_bytes() != sizeof(BObsHost) || gather_term_bytes() != sizeof(Term))
+    if (bpass_bytes() != sizeof(BPassHost) || bobs_bytes() != sizeof(BObsHost) || gather_term_bytes() != sizeof(Term) ||
+        bparam_bytes() != sizeof(BParamHost))
         return set_error(QF_ERR_CUDA, "batch table layout mismatch");
     std::vector<unsigned char> host(sz, 0);
     auto put = [&](size_t at, const void *src, size_t n) {
@@ -462,6 +475,7 @@ static qf_status build_t(qf_batch *b) {
     put(o_ops, ops.data(), ops.size() * sizeof(TOp));
     put(o_pool, pool.data(), pool.size() * sizeof(C));
     put(o_stg, stages.data(), stages.size() * sizeof(TStage));
+    put(o_prec, precs.data(), precs.size() * sizeof(BParamHost));
     put(o_obs, obs.data(), obs.size() * sizeof(BObsHost));
     put(o_opref, oprefix.data(), oprefix.size() * sizeof(long long));
     put(o_w, wts.data(), wts.size() * sizeof(double));
@@ -519,8 +533,12 @@ static qf_status build_t(qf_batch *b) {
         QF_CUDA(cudaStreamBeginCapture(b->bstream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = cudaSuccess;
         {
-            e = launch_batch_init<R>(b->bstream, b->sms, states, psi_elems, reinterpret_cast<const long long *>(tab + o_one),
-                                     nc);
+            e = launch_batch_resolve<R>(b->bstream, b->sms, reinterpret_cast<C *>(tab + o_pool), tab + o_prec,
+                                        (int)precs.size(), b->d_params);
+            nl += precs.empty() ? 0 : 1;
+            if (e == cudaSuccess)
+                e = launch_batch_init<R>(b->bstream, b->sms, states, psi_elems,
+                                         reinterpret_cast<const long long *>(tab + o_one), nc);
             nl += 2;
         }
         for (const LaunchRec &L : fwd) {

@@ -116,3 +116,35 @@ def test_batch_full_size_sample(orc):
     qf.qf_batch_free(b)
     for p in progs:
         qf.qf_program_free(p)
+
+
+def test_autotuned_batch_matches(tmp_path):
+    """The autotuner picks a tile size and fusion depth per d from timed
+    candidates; the tuned batch gives the same losses and gradients."""
+    qf = gpu_lib()
+    from paper_2409_17716_gb300 import autotune
+    circuits, params = W.batch_circuits(count=24, seed=77, n_range=(3, 8))
+    tuning = autotune.tune(circuits, params, qf.QF_C64, sample=4, cache_path=str(tmp_path / "tune.json"))
+    assert set(tuning) == {c.d for c in circuits}
+    for d, t in tuning.items():
+        assert (t["tile_qudits"], t["max_ops"]) in autotune.candidates(d, False)
+        assert len(t["tried"]) == len(autotune.candidates(d, False))
+    w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
+    results = []
+    for tuned in (False, True):
+        b = qf.qf_batch_create(qf.QF_C64)
+        progs = [qf.program_from_ops(c.d, c.n, c.ops) for c in circuits]
+        for p, c in zip(progs, circuits):
+            qf.qf_batch_add(b, p, w0(c))
+        if tuned:
+            autotune.apply(b, tuning)
+        qf.qf_batch_build(b, len(params))
+        qf.qf_batch_run(b, params, True)
+        results.append(qf.qf_batch_read(b))
+        qf.qf_batch_free(b)
+        for p in progs:
+            qf.qf_program_free(p)
+    (l0, g0, s0), (l1, g1, s1) = results
+    np.testing.assert_allclose(l1, l0, atol=2e-6)
+    np.testing.assert_allclose(g1, g0, atol=2e-5)
+    np.testing.assert_allclose(s1, s0, atol=1e-4)
