@@ -52,12 +52,12 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
 
     // stage the gate list, matrix pool and run offsets
     const C *msrc = A.mat_g ? A.mat_g : A.mat_i;
-    for (int i = tid; i < A.nmat; i += kTileBlock) mats[i] = msrc[i];
+    for (int i = tid; i < A.nmat; i += blockDim.x) mats[i] = msrc[i];
     if (A.ops_g) {
         const int *src = reinterpret_cast<const int *>(A.ops_g);
         int *dst = reinterpret_cast<int *>(ops);
         const int words = A.nops * (int)(sizeof(TOp) / sizeof(int));
-        for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
+        for (int i = tid; i < words; i += blockDim.x) dst[i] = src[i];
     } else if (tid == 0) {
         ops[0] = A.op_i;
     }
@@ -65,9 +65,9 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
         const int *src = reinterpret_cast<const int *>(A.stages_g);
         int *dst = reinterpret_cast<int *>(stages);
         const int words = A.nstages * (int)(sizeof(TStage) / sizeof(int));
-        for (int i = tid; i < words; i += kTileBlock) dst[i] = src[i];
+        for (int i = tid; i < words; i += blockDim.x) dst[i] = src[i];
     }
-    for (int a = tid; a < nA; a += kTileBlock) {
+    for (int a = tid; a < nA; a += blockDim.x) {
         long long off = 0;
         int rem = a;
         for (int i = g.kA - 1; i >= 0; --i) {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
     for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const long long base = sbase[0];
         const C *src = A.psi + base;
-        for (int e = tid; e < T; e += kTileBlock) {
+        for (int e = tid; e < T; e += blockDim.x) {
             int a = (int)g.divSEG.div((uint32_t)e);
             int lo = e - a * g.SEG;
             cp_async_amp<R>(tile + e, src + offA[a] + lo);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
             }
         }
         C *dst = A.psi + base;
-        for (int e = tid; e < T; e += kTileBlock) {
+        for (int e = tid; e < T; e += blockDim.x) {
             int a = (int)g.divSEG.div((uint32_t)e);
             int lo = e - a * g.SEG;
             dst[offA[a] + lo] = tile[e];
@@ -135,13 +135,22 @@ static cudaError_t launch_tile_d(const Launch &L, const TileArgs<R> &A, int d, s
         if (e != cudaSuccess) return e;
         configured_bytes = (int)smem;
     }
+    // a tile with fewer register blocks than a 256-thread CTA runs on 128
+    // threads (every loop of the kernel strides by blockDim.x)
+    int threads = kTileBlock;
+    const int K = stage_k(d, false, sizeof(R) == 8);
+    if (A.nstages > 0 && K > 0) {
+        int dk = 1;
+        for (int i = 0; i < K; ++i) dk *= d;
+        if (A.g.T / dk < kTileBlock) threads = kTileBlock / 2;
+    }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, D>, kTileBlock, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, D>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long grid = (long long)per_sm * L.num_sms;
     if (grid > A.g.ntiles) grid = A.g.ntiles;
-    k_tile<R, D><<<(unsigned)grid, kTileBlock, smem, L.stream>>>(A, d);
+    k_tile<R, D><<<(unsigned)grid, threads, smem, L.stream>>>(A, d);
     return cudaGetLastError();
 }
 

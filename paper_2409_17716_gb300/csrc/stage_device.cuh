@@ -323,7 +323,7 @@ __device__ __forceinline__ void stage_run(const TStage &st, const TOp *ops, cons
                                           cplx<R> *tl, int T, R *gsum) {
     constexpr int DK = cpow(D, K);
     const int nblk = T / DK;
-    for (int blk = threadIdx.x; blk < nblk; blk += kTileBlock) {
+    for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
         // insert a zero digit at every slot stride (ascending)
         int base = blk;
 #pragma unroll

@@ -109,7 +109,7 @@ __device__ void tile_apply(const TOp &op, cplx<R> *tile, const cplx<R> *mats, in
     case OP_SWAP: {
         // exchange the digits of local qudits a (stride lsa) and c (stride lsc)
         const int la = op.lsa, lc = op.lsc;
-        for (int e = tid; e < T; e += kTileBlock) {
+        for (int e = tid; e < T; e += blockDim.x) {
             int x = dmod<D>(op.fa.div((uint32_t)e), d);
             int y = dmod<D>(op.fc.div((uint32_t)e), d);
             if (x < y) {
@@ -138,7 +138,7 @@ __device__ void tile_apply(const TOp &op, cplx<R> *tile, const cplx<R> *mats, in
                 int t = asc[m]; asc[m] = asc[m - 1]; asc[m - 1] = t;
             }
         const int G = T / DK;
-        for (int g = tid; g < G; g += kTileBlock) {
+        for (int g = tid; g < G; g += blockDim.x) {
             // insert a zero digit at every target stride (ascending)
             int b = g;
             for (int i = 0; i < K; ++i) b = (b / asc[i]) * (asc[i] * d) + b % asc[i];
@@ -163,7 +163,7 @@ __device__ void tile_apply(const TOp &op, cplx<R> *tile, const cplx<R> *mats, in
         const int ls = op.lsa;
         const int F = T / d;
         const bool ctrl = op.kind == OP_CPAIR || op.kind == OP_CDIAG || op.kind == OP_CSHIFT;
-        for (int f = tid; f < F; f += kTileBlock) {
+        for (int f = tid; f < F; f += blockDim.x) {
             int hi = (int)op.fa.div((uint32_t)f);
             int b = hi * d * ls + (f - hi * ls);
             int ctl = ctrl ? dmod<D>(op.fc.div((uint32_t)b), d) : 0;
