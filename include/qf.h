@@ -159,6 +159,17 @@ qf_status qf_apply_h(qf_state *s, int q);
  * memory out_host.  Synchronises the state's stream. */
 qf_status qf_expect(qf_state *s, const qf_obs *obs, double *out_host);
 
+/* Measurement (section "Code style": measure(state, index, ..., shots)
+ * returns a histogram and the probabilities of the measured qudits).
+ * probs (host, d^k doubles): marginal probability of every joint level r of
+ * the k qudits idx[0..k-1] (idx[0] most significant digit of r), summed in
+ * FP64.  With shots > 0, counts (host, d^k int64) is the histogram of `shots`
+ * samples: sample s falls in the first r whose cumulative probability exceeds
+ * uniforms[s] times the total (uniforms: host, shots values in [0, 1), drawn
+ * by the caller).  Requires d^k <= 16384.  Synchronises the state's stream. */
+qf_status qf_measure(qf_state *s, const int *idx, int k, const double *uniforms, long long shots, double *probs,
+                     long long *counts);
+
 /* As qf_expect, but writes the FP64 results to device memory out_dev
  * (8-byte aligned) asynchronously on the state's stream. */
 qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev);

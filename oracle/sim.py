@@ -266,3 +266,14 @@ def grad_fd(ops, d: int, n: int, params, weights, h: float = 1e-5, psi0=None, sl
         lm = loss(run(ops, d, n, psi0, tm), d, n, weights)
         out.append((lp - lm) / (2.0 * h))
     return np.array(out)
+
+
+def sample(probs, uniforms) -> np.ndarray:
+    """Histogram of samples from a discrete distribution by its inverse
+    CDF: sample s falls in the first bin whose cumulative probability exceeds
+    uniforms[s] times the total."""
+    probs = np.asarray(probs, dtype=float)
+    cdf = np.cumsum(probs)
+    x = np.asarray(uniforms, dtype=float) * cdf[-1]
+    idx = np.searchsorted(cdf, x, side="right")
+    return np.bincount(np.minimum(idx, len(probs) - 1), minlength=len(probs)).astype(np.int64)

@@ -413,3 +413,110 @@ extern "C" qf_status qf_expect_number_noalloc(const void *psi_dev, int d, int n,
     if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: reduction kernels");
     return QF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Measurement ("Code style": measure(state, index, ..., shots) returns the
+// marginal probabilities of the `index` qudits and a histogram of shots).
+namespace qf {
+
+struct MargArgs {
+    int k;                        // measured qudits
+    long long stride[kMaxQudits];  // global strides of the measured qudits, most significant first
+    int bins;                     // d^k
+};
+
+// Per-CTA bins in shared memory (FP64 atomics, so the order of additions within
+// a CTA -- and the last bits of a bin -- may vary between runs), one row of
+// partials per CTA, summed in CTA order.
+template <typename R>
+__global__ void __launch_bounds__(256) k_marginal(const cplx<R> *__restrict__ psi, int d, long long N,
+                                                   const __grid_constant__ MargArgs M, double *partials) {
+    extern __shared__ double bins[];
+    for (int b = threadIdx.x; b < M.bins; b += blockDim.x) bins[b] = 0.0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        const cplx<R> v = psi[i];
+        const double p = (double)v.x * v.x + (double)v.y * v.y;
+        int r = 0;
+        for (int a = 0; a < M.k; ++a) r = r * d + (int)((i / M.stride[a]) % d);
+        atomicAdd(&bins[r], p);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < M.bins; b += blockDim.x) partials[(long long)blockIdx.x * M.bins + b] = bins[b];
+}
+
+// Shots: shot s lands in the first bin whose cumulative probability exceeds
+// u_s (inverse CDF of the marginal; u_s uniform in [0, 1), supplied).
+__global__ void k_sample(const double *cdf, int bins, const double *u, long long shots, unsigned long long *counts) {
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < shots; s += (long long)gridDim.x * blockDim.x) {
+        const double x = u[s] * cdf[bins - 1];
+        int lo = 0, hi = bins - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cdf[mid] > x) hi = mid;
+            else lo = mid + 1;
+        }
+        atomicAdd(&counts[lo], 1ull);
+    }
+}
+
+// Inclusive prefix sum of the marginal, one thread, in bin order.
+__global__ void k_cdf(const double *marg, int bins, double *cdf) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < bins; ++b) {
+            s += marg[b];
+            cdf[b] = s;
+        }
+    }
+}
+
+constexpr int kMargBlocks = 64;
+
+template <typename R>
+cudaError_t launch_marginal(const Launch &L, const cplx<R> *psi, int d, int n, const int *idx, int k, double *partials,
+                            double *out_dev) {
+    MargArgs M;
+    M.k = k;
+    M.bins = 1;
+    for (int a = 0; a < k; ++a) {
+        long long s = 1;
+        for (int i = 0; i < n - 1 - idx[a]; ++i) s *= d;
+        M.stride[a] = s;
+        M.bins *= d;
+    }
+    long long N = 1;
+    for (int i = 0; i < n; ++i) N *= d;
+    long long b = (N + 255) / 256;
+    int blocks = (int)(b < kMargBlocks ? b : kMargBlocks);
+    const size_t smem = (size_t)M.bins * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_marginal<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_marginal<R><<<blocks, 256, smem, L.stream>>>(psi, d, N, M, partials);
+    k_sum_partials<<<1, 256, 0, L.stream>>>(partials, blocks, M.bins, out_dev);
+    return cudaGetLastError();
+}
+
+int marginal_max_blocks() { return kMargBlocks; }
+
+cudaError_t launch_sample(const Launch &L, const double *marg, int bins, double *cdf, const double *u, long long shots,
+                          unsigned long long *counts) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)bins * sizeof(unsigned long long), L.stream);
+    if (e != cudaSuccess) return e;
+    k_cdf<<<1, 32, 0, L.stream>>>(marg, bins, cdf);
+    if (shots > 0) {
+        long long b = (shots + 255) / 256;
+        int blocks = (int)(b < 4LL * L.num_sms ? b : 4LL * L.num_sms);
+        k_sample<<<blocks, 256, 0, L.stream>>>(cdf, bins, u, shots, counts);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_marginal<float>(const Launch &, const cplx<float> *, int, int, const int *, int, double *,
+                                            double *);
+template cudaError_t launch_marginal<double>(const Launch &, const cplx<double> *, int, int, const int *, int, double *,
+                                             double *);
+
+}  // namespace qf

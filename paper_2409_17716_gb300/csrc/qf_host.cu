@@ -229,6 +229,7 @@ qf_status qf_state_free(qf_state *s) {
     if (s->h_up) cudaFreeHost(s->h_up);
     if (s->d_up) cudaFree(s->d_up);
     if (s->up_ev) cudaEventDestroy(s->up_ev);
+    if (s->d_meas) cudaFree(s->d_meas);
     delete s;
     return QF_OK;
 }
@@ -376,6 +377,51 @@ qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev) {
         return set_error(QF_ERR_ARG, "unknown observable kind");
     }
     if (e != cudaSuccess) return cuda_error(e, "reduction kernels");
+    return QF_OK;
+}
+
+qf_status qf_measure(qf_state *s, const int *idx, int k, const double *uniforms, long long shots, double *probs,
+                     long long *counts) {
+    if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
+    if (!idx || k < 1 || k > s->n) return set_error(QF_ERR_ARG, "need 1 <= k <= n measured qudits");
+    for (int a = 0; a < k; ++a) {
+        if (idx[a] < 0 || idx[a] >= s->n) return set_error(QF_ERR_ARG, "measured qudit out of range");
+        for (int b = 0; b < a; ++b)
+            if (idx[a] == idx[b]) return set_error(QF_ERR_ARG, "measured qudits must be distinct");
+    }
+    long long bins = ipow_ll(s->d, k);
+    if (bins > 16384) return set_error(QF_ERR_UNSUPPORTED, "measure: d^k must be <= 16384");
+    if (shots < 0 || (shots > 0 && (!uniforms || !counts))) return set_error(QF_ERR_ARG, "bad shots / uniforms / counts");
+    if (!probs) return set_error(QF_ERR_ARG, "probs is NULL");
+    const size_t need = (size_t)marginal_max_blocks() * bins * 8 + 2 * bins * 8 + bins * 8 + (size_t)shots * 8 + 256;
+    if (need > s->meas_cap) {
+        QF_CUDA(cudaStreamSynchronize(s->stream));
+        if (s->d_meas) cudaFree(s->d_meas);
+        s->d_meas = nullptr;
+        s->meas_cap = 0;
+        if (cudaMalloc(&s->d_meas, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "measurement scratch allocation failed");
+        }
+        s->meas_cap = need;
+    }
+    double *part = reinterpret_cast<double *>(s->d_meas);
+    double *pr = part + (size_t)marginal_max_blocks() * bins;
+    double *cdf = pr + bins;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(cdf + bins);
+    double *u = reinterpret_cast<double *>(cnt + bins);
+    const Launch L = launch_of(s);
+    if (shots > 0) QF_CUDA(cudaMemcpyAsync(u, uniforms, (size_t)shots * 8, cudaMemcpyHostToDevice, s->stream));
+    cudaError_t e = s->dt == QF_C64 ? launch_marginal<float>(L, (const float2 *)s->data, s->d, s->n, idx, k, part, pr)
+                                    : launch_marginal<double>(L, (const double2 *)s->data, s->d, s->n, idx, k, part, pr);
+    if (e != cudaSuccess) return cuda_error(e, "marginal kernels");
+    if (shots > 0) {
+        e = launch_sample(L, pr, (int)bins, cdf, u, shots, cnt);
+        if (e != cudaSuccess) return cuda_error(e, "sampling kernels");
+    }
+    QF_CUDA(cudaMemcpyAsync(probs, pr, (size_t)bins * 8, cudaMemcpyDeviceToHost, s->stream));
+    if (shots > 0) QF_CUDA(cudaMemcpyAsync(counts, cnt, (size_t)bins * 8, cudaMemcpyDeviceToHost, s->stream));
+    QF_CUDA(cudaStreamSynchronize(s->stream));
     return QF_OK;
 }
 

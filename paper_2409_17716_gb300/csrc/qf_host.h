@@ -29,6 +29,12 @@ cudaError_t launch_fibre_reduce(const Launch &L, const cplx<R> *psi, int d, int 
                                 double *partials, double *out_dev);
 int reduce_max_blocks(int num_sms);
 template <typename R>
+cudaError_t launch_marginal(const Launch &L, const cplx<R> *psi, int d, int n, const int *idx, int k, double *partials,
+                            double *out_dev);
+int marginal_max_blocks();
+cudaError_t launch_sample(const Launch &L, const double *marg, int bins, double *cdf, const double *u, long long shots,
+                          unsigned long long *counts);
+template <typename R>
 cudaError_t launch_number_obs(const Launch &L, const cplx<R> *psi, cplx<R> *lam, int d, int n, const double *w,
                               double *partials, double *loss_dev);
 template <typename R>
@@ -138,4 +144,7 @@ struct qf_state {
     size_t up_cap = 0;
     cudaEvent_t up_ev = nullptr;
     bool up_pending = false;
+    // measurement scratch (marginal partials, probabilities, CDF, counts, uniforms)
+    void *d_meas = nullptr;
+    size_t meas_cap = 0;
 };

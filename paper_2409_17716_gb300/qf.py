@@ -61,6 +61,8 @@ _PROTOS = {
     "qf_expect": (_int, [_vp, _c.POINTER(qf_obs), _c.POINTER(_dbl)]),
     "qf_expect_device": (_int, [_vp, _c.POINTER(qf_obs), _vp]),
     "qf_expect_number_noalloc": (_int, [_vp, _int, _int, _int, _vp, _vp]),
+    "qf_measure": (_int, [_vp, _c.POINTER(_int), _int, _c.POINTER(_dbl), _c.c_longlong, _c.POINTER(_dbl),
+                          _c.POINTER(_c.c_longlong)]),
     "qf_program_create": (_int, [_int, _int, _c.POINTER(_vp)]),
     "qf_program_free": (_int, [_vp]),
     "qf_program_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int)]),
@@ -255,6 +257,24 @@ def qf_expect_device(s: int, out_dev_ptr: int, kind: int = QF_OBS_NUMBER_ALL, q:
     o, keep = _obs(kind, q, matrix)
     _call("qf_expect_device", s, _c.byref(o), out_dev_ptr)
     del keep
+
+
+def qf_measure(s: int, index: Sequence[int], shots: int = 0, uniforms=None, seed: int = 0):
+    """(histogram, probabilities) of the qudits in `index` (the paper's
+    measure()).  Shots use `uniforms` if given, else uniforms drawn from a
+    seeded numpy generator (input generation, not simulation)."""
+    d, n, _ = qf_state_info(s)
+    k = len(index)
+    bins = d ** k
+    idx = (_int * k)(*[int(x) for x in index])
+    probs = np.zeros(bins)
+    counts = np.zeros(bins, dtype=np.int64)
+    if shots and uniforms is None:
+        uniforms = np.random.default_rng(seed).random(shots)
+    u = _f64(uniforms) if shots else np.zeros(1)
+    _call("qf_measure", s, idx, k, _dptr(u), int(shots), _dptr(probs),
+          counts.ctypes.data_as(_c.POINTER(_c.c_longlong)))
+    return (counts if shots else None), probs
 
 
 def qf_expect_number_noalloc(psi_dev_ptr: int, d: int, n: int, dtype: int, out_dev_ptr: int, stream=None) -> None:
