@@ -225,6 +225,15 @@ qf_status qf_program_add_h(qf_program *p, int q);
  * effect at the next run. */
 qf_status qf_program_set_fusion(qf_program *p, int enable);
 
+/* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
+ * per shared-memory tile (capped by the default, d^t amplitudes <= 8192 for
+ * complex64 / 4096 for complex128); min_run_qudits = lowest qudits always in
+ * the tile, so every contiguous run read from HBM has d^r amplitudes (default
+ * 5, 3, 2, 1 for d = 2, 3, 4, 5, chosen by measurement; otherwise the smallest
+ * r with d^r >= 32); max_ops = gates per pass (<= 96).  Takes
+ * effect at the next run. */
+qf_status qf_program_set_tiling(qf_program *p, int tile_qudits, int min_run_qudits, int max_ops);
+
 /* Applies the program to s (same d and n).  params: host FP64 vector of
  * at least num_params entries (may be NULL if num_params == 0).  Async. */
 qf_status qf_program_run(qf_program *p, qf_state *s, const double *params);

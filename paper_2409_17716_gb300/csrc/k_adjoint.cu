@@ -250,6 +250,9 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
     double *gacc = reinterpret_cast<double *>(smem + off);
     long long *offA = reinterpret_cast<long long *>(gacc + (size_t)A.nops * kAdjWarps);
     long long *sbase = offA + nA;
+    float4 *prep = reinterpret_cast<float4 *>(
+        smem + ((off + (size_t)A.nops * kAdjWarps * sizeof(double) + (size_t)(nA + 1) * sizeof(long long) + 15) &
+                ~(size_t)15));
 
     for (int i = tid; i < A.nmat; i += kTileBlock) mats[i] = A.mats[i];
     {
@@ -279,15 +282,19 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
     }
     if (tid == 0) sbase[0] = tile_base(g, blockIdx.x);
     __syncthreads();
+    if (A.nstages > 0) prepare_pool<R>(mats, prep, A.nmat);
+    const int a0 = (int)g.divSEG.div((uint32_t)tid), lo0 = tid - a0 * g.SEG;
+    const int da = (int)g.divSEG.div((uint32_t)kTileBlock), dl = kTileBlock - da * g.SEG;
 
     for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const long long base = sbase[0];
-        for (int e = tid; e < T; e += kTileBlock) {
-            int a = (int)g.divSEG.div((uint32_t)e);
-            int lo = e - a * g.SEG;
+        for (int e = tid, a = a0, lo = lo0; e < T; e += kTileBlock) {
             const long long gi = base + offA[a] + lo;
             cp_async_amp<R>(tp + e, A.psi + gi);
             cp_async_amp<R>(tl + e, A.lam + gi);
+            lo += dl;
+            a += da;
+            if (lo >= g.SEG) { lo -= g.SEG; ++a; }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
                 for (int si = 0; si < A.nstages; ++si) {
                     const TStage &st = stages[si];
                     if (!st.legacy) {
-                        stage_run<R, D, StageK<R, D, true>::K, true>(st, ops, mats, tp, tl, T, gsum);
+                        stage_run<R, D, StageK<R, D, true>::K, true>(st, ops, mats, prep, tp, tl, T, gsum);
                     } else {
                         // SWAP / custom gates: no angle
                         tile_apply<R, D>(ops[st.first], tp, mats, T, g.nt, d);
@@ -334,12 +341,13 @@ __global__ void __launch_bounds__(kTileBlock) k_tile_adj(const __grid_constant__
             (void)M;
         }
     store:
-        for (int e = tid; e < T; e += kTileBlock) {
-            int a = (int)g.divSEG.div((uint32_t)e);
-            int lo = e - a * g.SEG;
+        for (int e = tid, a = a0, lo = lo0; e < T; e += kTileBlock) {
             const long long gi = base + offA[a] + lo;
             A.psi[gi] = tp[e];
             A.lam[gi] = tl[e];
+            lo += dl;
+            a += da;
+            if (lo >= g.SEG) { lo -= g.SEG; ++a; }
         }
         if (tid == 0 && t + gridDim.x < g.ntiles) sbase[0] = tile_base(g, t + gridDim.x);
         __syncthreads();
@@ -379,7 +387,9 @@ size_t adj_smem_bytes(const TileGeom &g, int nops, int nmat, int nstages) {
                (size_t)nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
     b += (size_t)nops * kAdjWarps * sizeof(double);
-    b += (size_t)(g.T / g.SEG) * sizeof(long long) + 16;
+    b += (size_t)(g.T / g.SEG + 1) * sizeof(long long);
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)nmat * sizeof(float4);   // prepared entries (complex64 register stages)
     return b;
 }
 

@@ -134,6 +134,10 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
     double *gacc = reinterpret_cast<double *>(smem + off);
     long long *offA = reinterpret_cast<long long *>(gacc + (ADJ ? (size_t)A.max_nops * kBatchWarps : 0));
     long long *sbase = offA + A.max_nA;
+    float4 *prep = reinterpret_cast<float4 *>(
+        smem + ((off + (ADJ ? (size_t)A.max_nops * kBatchWarps * sizeof(double) : 0) +
+                 (size_t)(A.max_nA + 1) * sizeof(long long) + 15) &
+                ~(size_t)15));
 
     const long long total = A.prefix[A.npasses];
     int cur = -1;
@@ -170,6 +174,10 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
                 }
                 offA[a] = o;
             }
+            if (P.nstages > 0) {
+                __syncthreads();   // pool staged before it is prepared
+                prepare_pool<R>(mats, prep, P.nmat);
+            }
             cur = k;
         }
         if (ADJ)
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(kTileBlock) k_batch(const __grid_constant__ Ba
                     for (int si = 0; si < P.nstages; ++si) {
                         const TStage &st = stages[si];
                         if (!st.legacy) {
-                            stage_run<R, D, KS, ADJ>(st, ops, mats, tp, tl, T, gsum);
+                            stage_run<R, D, KS, ADJ>(st, ops, mats, prep, tp, tl, T, gsum);
                         } else {
                             tile_apply<R, D>(ops[st.first], tp, mats, T, g.nt, d);
                             if (ADJ) tile_apply<R, D>(ops[st.first], tl, mats, T, g.nt, d);
@@ -278,7 +286,9 @@ size_t batch_smem_bytes(bool adj, int max_T, int max_nmat, int max_nops, int max
                (size_t)max_nops * sizeof(TOp) + (size_t)max_nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
     if (adj) b += (size_t)max_nops * kBatchWarps * sizeof(double);
-    b += (size_t)max_nA * sizeof(long long) + 16;
+    b += (size_t)(max_nA + 1) * sizeof(long long);
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)max_nmat * sizeof(float4);   // prepared entries (complex64 register stages)
     return b;
 }
 

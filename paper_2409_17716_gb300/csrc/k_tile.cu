@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
     off = (off + 15) & ~(size_t)15;
     long long *offA = reinterpret_cast<long long *>(smem + off);
     long long *sbase = offA + nA;
+    float4 *prep = reinterpret_cast<float4 *>(smem + ((off + (size_t)(nA + 1) * sizeof(long long) + 15) & ~(size_t)15));
 
     // stage the gate list, matrix pool and run offsets
     const C *msrc = A.mat_g ? A.mat_g : A.mat_i;
@@ -78,14 +79,19 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
     }
     if (tid == 0) sbase[0] = tile_base(g, blockIdx.x);
     __syncthreads();
+    if (A.nstages > 0) prepare_pool<R>(mats, prep, A.nmat);
+    // element e = a * SEG + lo of the tile; each thread steps by blockDim.x
+    const int a0 = (int)g.divSEG.div((uint32_t)tid), lo0 = tid - a0 * g.SEG;
+    const int da = (int)g.divSEG.div((uint32_t)blockDim.x), dl = (int)blockDim.x - da * g.SEG;
 
     for (long long t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         const long long base = sbase[0];
         const C *src = A.psi + base;
-        for (int e = tid; e < T; e += blockDim.x) {
-            int a = (int)g.divSEG.div((uint32_t)e);
-            int lo = e - a * g.SEG;
+        for (int e = tid, a = a0, lo = lo0; e < T; e += blockDim.x) {
             cp_async_amp<R>(tile + e, src + offA[a] + lo);
+            lo += dl;
+            a += da;
+            if (lo >= g.SEG) { lo -= g.SEG; ++a; }
         }
         cp_async_wait_all();
         __syncthreads();
@@ -94,7 +100,7 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
                 const TStage &st = stages[si];
                 if constexpr (StageK<R, D, false>::K > 0) {
                     if (!st.legacy)
-                        stage_run<R, D, StageK<R, D, false>::K, false>(st, ops, mats, tile, nullptr, T, nullptr);
+                        stage_run<R, D, StageK<R, D, false>::K, false>(st, ops, mats, prep, tile, nullptr, T, nullptr);
                     else tile_apply<R, D>(ops[st.first], tile, mats, T, g.nt, d);
                 } else {
                     tile_apply<R, D>(ops[st.first], tile, mats, T, g.nt, d);
@@ -108,10 +114,11 @@ __global__ void __launch_bounds__(kTileBlock) k_tile(const __grid_constant__ Til
             }
         }
         C *dst = A.psi + base;
-        for (int e = tid; e < T; e += blockDim.x) {
-            int a = (int)g.divSEG.div((uint32_t)e);
-            int lo = e - a * g.SEG;
+        for (int e = tid, a = a0, lo = lo0; e < T; e += blockDim.x) {
             dst[offA[a] + lo] = tile[e];
+            lo += dl;
+            a += da;
+            if (lo >= g.SEG) { lo -= g.SEG; ++a; }
         }
         if (tid == 0 && t + gridDim.x < g.ntiles) sbase[0] = tile_base(g, t + gridDim.x);
         __syncthreads();
@@ -123,7 +130,9 @@ size_t tile_smem_bytes(const TileGeom &g, int nops, int nmat, int nstages) {
     size_t b = (size_t)g.T * sizeof(cplx<R>) + (size_t)nmat * sizeof(cplx<R>) + (size_t)nops * sizeof(TOp) +
                (size_t)nstages * sizeof(TStage);
     b = (b + 15) & ~(size_t)15;
-    b += (size_t)(g.T / g.SEG) * sizeof(long long) + 16;
+    b += (size_t)(g.T / g.SEG + 1) * sizeof(long long);
+    b = (b + 15) & ~(size_t)15;
+    b += (size_t)nmat * sizeof(float4);   // prepared entries (complex64 register stages)
     return b;
 }
 

@@ -153,6 +153,7 @@ ROp resolve_gate(const HGate &g, int d, double th) {
         o.k = g.k;
         if (g.axis == 'x' || g.axis == 'y') {
             o.kind = OP_PAIR;
+            o.s = g.axis == 'y' ? 1 : 0;   // 1: real 2x2 block
             r.m.resize(4);
         } else {
             o.kind = OP_DIAG;
@@ -168,6 +169,7 @@ ROp resolve_gate(const HGate &g, int d, double th) {
         o.k = g.k;
         const bool pair = g.axis == 'x' || g.axis == 'y';
         o.kind = pair ? OP_CPAIR : OP_CDIAG;
+        o.s = g.axis == 'y' ? 1 : 0;       // 1: real 2x2 blocks
         const int per = pair ? 4 : d;
         r.m.resize((size_t)per * d);
         for (int m = 0; m < d; ++m) rot_entries(d, g.j, g.k, g.axis, m * th, r.m.data() + per * m, &o.mask);
@@ -235,14 +237,28 @@ int default_tile_qudits(int d, bool c128) {
     return nt;
 }
 
+// Lowest qudits always kept in a tile, so every run a tile reads from HBM
+// is d^r contiguous amplitudes.  Longer runs read HBM more efficiently, shorter
+// ones leave room for more active qudits (more gates per pass).  Measured on
+// GB300 with 200-gate random circuits: d=2 keeps 32-amplitude runs, d=3 27 or
+// 81 (equal), d=4 is 13% faster with 16-amplitude runs than with 64, d=5 15%
+// faster with 5-amplitude runs (14 passes instead of 31) than with 125.
 int min_low_qudits(int d) {
-    int r = 0;
-    long long t = 1;
-    while (t < 32) {
-        t *= d;
-        ++r;
+    switch (d) {
+    case 2: return 5;
+    case 3: return 3;
+    case 4: return 2;
+    case 5: return 1;
+    default: {
+        int r = 0;
+        long long t = 1;
+        while (t < 32) {
+            t *= d;
+            ++r;
+        }
+        return r;
     }
-    return r;
+    }
 }
 
 TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL) {
@@ -318,12 +334,12 @@ static int fit_rl(const std::vector<bool> &inset, int n, int nt_max, int rl_min)
 }
 
 std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse, bool for_adjoint,
-                                  int nt_override, int max_ops) {
+                                  int nt_override, int max_ops, int rl_override) {
     std::vector<PassPlan> plan;
     int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
     if (nt_override > 0 && nt_override < nt_max) nt_max = nt_override;
     const int op_cap = (max_ops > 0 && max_ops < kMaxTileOps) ? max_ops : kMaxTileOps;
-    const int rl_min = std::min(min_low_qudits(d), nt_max);
+    const int rl_min = std::min(rl_override > 0 ? rl_override : min_low_qudits(d), nt_max);
     std::vector<int> remaining(gates.size());
     for (size_t i = 0; i < gates.size(); ++i) remaining[i] = (int)i;
     std::vector<int> qs;

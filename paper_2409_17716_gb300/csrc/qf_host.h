@@ -107,7 +107,7 @@ long long ipow_ll(int d, int e);
 // one pass per gate.  for_adjoint: tile passes only, and parametrised gates
 // are never multiplied into a group (each needs its own gradient).
 std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n, bool c128, bool fuse,
-                                  bool for_adjoint = false, int nt_override = 0, int max_ops = 0);
+                                  bool for_adjoint = false, int nt_override = 0, int max_ops = 0, int rl_override = 0);
 
 // Tile geometry for the given active qudits and low-qudit count.
 TileGeom make_geom(int d, int n, const std::vector<int> &active, int rL);

@@ -20,6 +20,7 @@ struct qf_program {
     int num_params = 0;
     bool fuse = true;
     bool stages = true;                // register stages in tile passes
+    int tile_qudits = 0, min_run_qudits = 0, max_ops = 0;   // planner overrides (0: default)
     bool plan_valid = false;
     bool plan_c128 = false;
     std::vector<PassPlan> plan;
@@ -222,7 +223,7 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
     if (!p->plan_valid || p->plan_c128 != c128) {
-        p->plan = plan_passes(p->gates, d, n, c128, p->fuse);
+        p->plan = plan_passes(p->gates, d, n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->plan_valid = true;
         p->plan_c128 = c128;
     }
@@ -332,7 +333,7 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
     if (!p->adj_valid || p->adj_c128 != c128) {
-        p->adj_plan = plan_passes(p->gates, d, n, c128, p->fuse, true);
+        p->adj_plan = plan_passes(p->gates, d, n, c128, p->fuse, true, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->adj_valid = true;
         p->adj_c128 = c128;
     }
@@ -574,6 +575,17 @@ qf_status qf_program_add_h(qf_program *p, int q) {
     return add(p, g);
 }
 
+qf_status qf_program_set_tiling(qf_program *p, int tile_qudits, int min_run_qudits, int max_ops) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (tile_qudits < 0 || min_run_qudits < 0 || max_ops < 0) return set_error(QF_ERR_ARG, "negative tiling value");
+    p->tile_qudits = tile_qudits;
+    p->min_run_qudits = min_run_qudits;
+    p->max_ops = max_ops;
+    p->plan_valid = false;
+    p->adj_valid = false;
+    return QF_OK;
+}
+
 qf_status qf_program_set_fusion(qf_program *p, int enable) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     p->fuse = enable != 0;
@@ -604,7 +616,7 @@ qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     const bool c128 = dt == QF_C128;
     if (!p->plan_valid || p->plan_c128 != c128) {
-        p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse);
+        p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->plan_valid = true;
         p->plan_c128 = c128;
     }

@@ -48,8 +48,19 @@ struct Fib {
     __host__ __device__ static constexpr int base(int f) { return (f / RS) * RS * D + f % RS; }
 };
 
+// Complex64 arithmetic on paired FP32 lanes: with a matrix entry prepared as
+// P = (re, re | -im, im), P.lo * a + P.hi * (a.y, a.x) is the complex product.
+__device__ __forceinline__ float2 pc_mul(const float4 &P, float2 a) {
+    const float2 r = __fmul2_rn(make_float2(P.x, P.y), a);
+    return __ffma2_rn(make_float2(P.z, P.w), make_float2(a.y, a.x), r);
+}
+__device__ __forceinline__ float2 pc_mac(const float4 &P, float2 a, float2 as, float2 acc) {
+    acc = __ffma2_rn(make_float2(P.x, P.y), a, acc);
+    return __ffma2_rn(make_float2(P.z, P.w), as, acc);
+}
+
 template <typename R, int D, int K, int S>
-__device__ __forceinline__ void reg_dense(cplx<R> *v, const cplx<R> *M) {
+__device__ __forceinline__ void reg_dense(cplx<R> *v, const cplx<R> *M, const float4 *P) {
     using F = Fib<D, K, S>;
 #pragma unroll
     for (int f = 0; f < F::NF; ++f) {
@@ -57,12 +68,25 @@ __device__ __forceinline__ void reg_dense(cplx<R> *v, const cplx<R> *M) {
         cplx<R> x[D];
 #pragma unroll
         for (int m = 0; m < D; ++m) x[m] = v[b + m * F::RS];
+        if constexpr (sizeof(R) == 4) {
+            float2 xs[D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            cplx<R> acc = cmul(M[l * D], x[0]);
+            for (int m = 0; m < D; ++m) xs[m] = make_float2(x[m].y, x[m].x);
 #pragma unroll
-            for (int m = 1; m < D; ++m) acc = cfma(M[l * D + m], x[m], acc);
-            v[b + l * F::RS] = acc;
+            for (int l = 0; l < D; ++l) {
+                float2 acc = pc_mul(P[l * D], x[0]);
+#pragma unroll
+                for (int m = 1; m < D; ++m) acc = pc_mac(P[l * D + m], x[m], xs[m], acc);
+                v[b + l * F::RS] = acc;
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                cplx<R> acc = cmul(M[l * D], x[0]);
+#pragma unroll
+                for (int m = 1; m < D; ++m) acc = cfma(M[l * D + m], x[m], acc);
+                v[b + l * F::RS] = acc;
+            }
         }
     }
 }
@@ -70,8 +94,10 @@ __device__ __forceinline__ void reg_dense(cplx<R> *v, const cplx<R> *M) {
 // 2x2 on levels (J, L) of slot S; control: CI = in-stage control slot or -1
 // (then ctl is the block's control level); controlled ops use M + 4 ctl and
 // skip ctl = 0.
+// real = true: the 2x2 block is real (RY-type; entries' imaginary parts
+// zero), so each output is two paired real scalings in complex64.
 template <typename R, int D, int K, int S, int J, int L, int CI>
-__device__ __forceinline__ void reg_pair(cplx<R> *v, const cplx<R> *M, bool ctrl, int ctl_block) {
+__device__ __forceinline__ void reg_pair(cplx<R> *v, const cplx<R> *M, bool ctrl, int ctl_block, bool real) {
     using F = Fib<D, K, S>;
 #pragma unroll
     for (int f = 0; f < F::NF; ++f) {
@@ -84,6 +110,14 @@ __device__ __forceinline__ void reg_pair(cplx<R> *v, const cplx<R> *M, bool ctrl
         }
         const cplx<R> *Mc = ctrl ? M + 4 * ctl : M;
         const cplx<R> a = v[b + J * F::RS], c = v[b + L * F::RS];
+        if constexpr (sizeof(R) == 4) {
+            if (real) {
+                const float m0 = Mc[0].x, m1 = Mc[1].x, m2 = Mc[2].x, m3 = Mc[3].x;
+                v[b + J * F::RS] = __ffma2_rn(make_float2(m1, m1), c, __fmul2_rn(make_float2(m0, m0), a));
+                v[b + L * F::RS] = __ffma2_rn(make_float2(m3, m3), c, __fmul2_rn(make_float2(m2, m2), a));
+                continue;
+            }
+        }
         v[b + J * F::RS] = cfma(Mc[1], c, cmul(Mc[0], a));
         v[b + L * F::RS] = cfma(Mc[3], c, cmul(Mc[2], a));
     }
@@ -246,13 +280,15 @@ __device__ __forceinline__ int block_digit(const FastDiv &f, int b) { return (in
 // Applies op to the register block v (psi) and, with ADJ, to w (lambda); with
 // ADJ and a parametrised op, returns its gradient term (before U^+ is applied).
 template <typename R, int D, int K, bool ADJ>
-__device__ __forceinline__ R reg_apply(const TOp &op, cplx<R> *v, cplx<R> *w, const cplx<R> *mats, int base) {
+__device__ __forceinline__ R reg_apply(const TOp &op, cplx<R> *v, cplx<R> *w, const cplx<R> *mats, const float4 *prep,
+                                       int base) {
     const cplx<R> *M = mats + op.mat;
+    const float4 *PM = prep + op.mat;
     const int sa = op_sa(op), sc = op_sc(op);
     R g = 0;
     switch (op.kind) {
     case OP_DENSE:
-        QF_FOR_SLOT(sa, { reg_dense<R, D, K, S>(v, M); if (ADJ) reg_dense<R, D, K, S>(w, M); })
+        QF_FOR_SLOT(sa, { reg_dense<R, D, K, S>(v, M, PM); if (ADJ) reg_dense<R, D, K, S>(w, M, PM); })
         break;
     case OP_PAIR:
     case OP_CPAIR: {
@@ -263,8 +299,8 @@ __device__ __forceinline__ R reg_apply(const TOp &op, cplx<R> *v, cplx<R> *w, co
         QF_FOR_SLOT(sa, QF_FOR_CI((ctrl ? sc : -1), QF_FOR_PAIR(p, {
             if (ADJ && op.gcol >= 0)
                 g = reg_grad_pair<R, D, K, S, PJ, PK, CI>(v, w, mats + op.gmat, ctrl, cb);
-            reg_pair<R, D, K, S, PJ, PK, CI>(v, M, ctrl, cb);
-            if (ADJ) reg_pair<R, D, K, S, PJ, PK, CI>(w, M, ctrl, cb);
+            reg_pair<R, D, K, S, PJ, PK, CI>(v, M, ctrl, cb, op.s == 1);
+            if (ADJ) reg_pair<R, D, K, S, PJ, PK, CI>(w, M, ctrl, cb, op.s == 1);
         })))
         break;
     }
@@ -318,9 +354,11 @@ __device__ __forceinline__ R reg_apply(const TOp &op, cplx<R> *v, cplx<R> *w, co
 
 // Runs one register stage over the tile(s).  gsum: per-thread gradient
 // accumulators indexed by op.gcol (ADJ only; summed in FP64 afterwards).
+// prep: complex64 pool entries prepared for paired FP32 arithmetic
+// (prepare_pool), unused for complex128.
 template <typename R, int D, int K, bool ADJ>
-__device__ __forceinline__ void stage_run(const TStage &st, const TOp *ops, const cplx<R> *mats, cplx<R> *tp,
-                                          cplx<R> *tl, int T, R *gsum) {
+__device__ __forceinline__ void stage_run(const TStage &st, const TOp *ops, const cplx<R> *mats, const float4 *prep,
+                                          cplx<R> *tp, cplx<R> *tl, int T, R *gsum) {
     constexpr int DK = cpow(D, K);
     const int nblk = T / DK;
     for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
@@ -342,7 +380,7 @@ __device__ __forceinline__ void stage_run(const TStage &st, const TOp *ops, cons
         }
         for (int oi = 0; oi < st.nops; ++oi) {
             const TOp &op = ops[st.first + oi];
-            const R g = reg_apply<R, D, K, ADJ>(op, v, w, mats, base);
+            const R g = reg_apply<R, D, K, ADJ>(op, v, w, mats, prep, base);
             if (ADJ && op.gcol >= 0) {
                 // register accumulators: compile-time indices
 #pragma unroll
@@ -359,6 +397,16 @@ __device__ __forceinline__ void stage_run(const TStage &st, const TOp *ops, cons
             if (ADJ) tl[base + o] = w[r];
         }
     }
+}
+
+// Pool entries (re, im) -> (re, re, -im, im) for paired FP32 arithmetic.
+template <typename R>
+__device__ __forceinline__ void prepare_pool(const cplx<R> *mats, float4 *prep, int nmat) {
+    if constexpr (sizeof(R) == 4)
+        for (int i = threadIdx.x; i < nmat; i += blockDim.x) {
+            const cplx<R> m = mats[i];
+            prep[i] = make_float4(m.x, m.x, -m.y, m.y);
+        }
 }
 
 }  // namespace qf

@@ -75,6 +75,7 @@ _PROTOS = {
     "qf_program_add_z": (_int, [_vp, _int, _int]),
     "qf_program_add_h": (_int, [_vp, _int]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
+    "qf_program_set_tiling": (_int, [_vp, _int, _int, _int]),
     "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
     "qf_program_last_passes": (_int, [_vp]),
     "qf_program_plan": (_int, [_vp, _int, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
@@ -333,6 +334,10 @@ def qf_program_add_z(p: int, q: int, power: int = 1) -> None:
 
 def qf_program_add_h(p: int, q: int) -> None:
     _call("qf_program_add_h", p, q)
+
+
+def qf_program_set_tiling(p: int, tile_qudits: int = 0, min_run_qudits: int = 0, max_ops: int = 0) -> None:
+    _call("qf_program_set_tiling", p, int(tile_qudits), int(min_run_qudits), int(max_ops))
 
 
 def qf_program_set_fusion(p: int, enable: bool) -> None:
