@@ -334,6 +334,8 @@ def main():
         line["adjoint"] = adjoint_bench(qf, W, torch, hbm_peak)
         torch.cuda.empty_cache()
         line["batched"] = batch_bench(qf, W, torch)
+        torch.cuda.empty_cache()
+        line["vqa_training"] = vqa_bench(qf, W, torch)
     if extras and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -533,6 +535,33 @@ def batch_bench(qf, W, torch):
             "autotuned": {str(d): {"tile_qudits": t["tile_qudits"], "max_ops": t["max_ops"]} for d, t in tuning.items()},
             "fd_per_circuit_ms_extrapolated": fd_total_ms, "speedup_vs_per_circuit_fd": fd_total_ms / t_fb,
             "note": "fd baseline: per-circuit fused forward + <N_q> on this GPU, (2P_c+1) runs, 64-circuit sample"}
+
+
+def vqa_bench(qf, W, torch):
+    """Training-step throughput of the paper's VQA circuits (rotation blocks
+    R1 / R2 / R3): 4096 samples per step (Iris-like d=3 n=4, MNIST-like d=10
+    n=2 and n=4), forward + adjoint of <N_0> in one graph replay, complex64."""
+    out = {}
+    for d, n in [(3, 4), (10, 2), (10, 4)]:
+        for variant in ("R1", "R2", "R3"):
+            circuits, params = W.vqa_batch(4096, d, n, variant)
+            b = qf.qf_batch_create(qf.QF_C64)
+            progs = []
+            for c in circuits:
+                p = qf.program_from_ops(c.d, c.n, c.ops)
+                qf.qf_batch_add(b, p, [1.0] + [0.0] * (c.n - 1))
+                progs.append(p)
+            qf.qf_batch_build(b, len(params))
+            qf.qf_batch_run(b, params, True)
+            ms = _time_ms(torch, lambda: qf.qf_batch_run(b, params, True), reps=3)
+            info = qf.qf_batch_info(b)
+            out["d%d_n%d_%s" % (d, n, variant)] = {
+                "samples_per_s": 4096 / (ms / 1e3), "step_ms": ms, "gates": len(circuits[0].ops),
+                "gradients_per_s": info["grad_local_len"] / (ms / 1e3)}
+            qf.qf_batch_free(b)
+            for p in progs:
+                qf.qf_program_free(p)
+    return out
 
 
 def e2e_throughput(qf, W, torch, sizes, progs, args):

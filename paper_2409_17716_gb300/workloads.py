@@ -29,6 +29,9 @@ Workload recipes (seeded; one master seed, each workload xors in its id):
     then a SUM ring or chain; parameter slots numbered layer, kind, qudit.
   * ``batch_circuits``    -- many small circuits of uneven d, n, L with
     per-sample encoding angles and a shared trainable-angle table.
+  * ``vqa_circuit`` / ``vqa_batch`` -- the paper's VQA circuit (Fourier,
+    RZ encoding, rotation block R1/R2/R3, CNOT fan-out from qudit 0, rotation
+    block) for a batch of samples with uniform stand-in encoding angles.
 """
 from __future__ import annotations
 
@@ -213,3 +216,68 @@ def uniform_state(d: int, n: int, seed: int = MASTER_SEED ^ 5) -> np.ndarray:
     N = d ** n
     v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
     return (v / np.linalg.norm(v)).astype(np.complex128)
+
+
+def rotation_block(d: int, n: int, variant: str, first_param: int) -> Tuple[List[Op], int]:
+    """One rotation block of the VQA circuit ("Variational quantum algorithm"
+    section), on every qudit, RX first, then RY, then RZ:
+      R1: level pair (0,1) for x, y and the level-pair z;
+      R2: x and y on pairs (0,k), k = 1..d-1; z as Gell-Mann S_z^j, j = 1..d-1;
+      R3: x and y on every pair (j,k); z as Gell-Mann S_z^j, j = 1..d-1.
+    Returns (ops, parameters used); slots are numbered from first_param in op order."""
+    if variant == "R1":
+        xy = [(0, 1)]
+    elif variant == "R2":
+        xy = [(0, k) for k in range(1, d)]
+    elif variant == "R3":
+        xy = [(j, k) for j in range(d) for k in range(j + 1, d)]
+    else:
+        raise ValueError(variant)
+    ops: List[Op] = []
+    p = first_param
+    for axis in ("x", "y"):
+        for (j, k) in xy:
+            for q in range(n):
+                ops.append(Op("rot", (q,), j=j, k=k, axis=axis, param=p))
+                p += 1
+    if variant == "R1":
+        for q in range(n):
+            ops.append(Op("rot", (q,), j=0, k=1, axis="z", param=p))
+            p += 1
+    else:
+        for j in range(1, d):
+            for q in range(n):
+                ops.append(Op("rot", (q,), j=j, axis="g", param=p))
+                p += 1
+    return ops, p - first_param
+
+
+def vqa_circuit(d: int, n: int, variant: str, enc_first: int, theta_first: int) -> Tuple[List[Op], int]:
+    """The VQA circuit of the paper's figure: Fourier on every qudit, RZ^{01}
+    data encoding (slots enc_first + q), a rotation block, CNOT (SUM) from
+    qudit 0 to every other qudit, a second rotation block.  Returns (ops,
+    trainable parameters used from theta_first)."""
+    ops: List[Op] = [Op("h", (q,)) for q in range(n)]
+    ops += [Op("rot", (q,), j=0, k=1, axis="z", param=enc_first + q) for q in range(n)]
+    b1, p1 = rotation_block(d, n, variant, theta_first)
+    ops += b1
+    ops += [Op("sum", (0, q)) for q in range(1, n)]
+    b2, p2 = rotation_block(d, n, variant, theta_first + p1)
+    ops += b2
+    return ops, p1 + p2
+
+
+def vqa_batch(count: int, d: int, n: int, variant: str, seed: int = MASTER_SEED ^ 6):
+    """`count` samples of one VQA circuit shape: per-sample encoding angles
+    U[0, pi) (stand-ins for the Iris / MNIST features the paper encodes) and
+    shared trainable angles N(0, 0.1).  Parameter vector = [trainable | n
+    encodings per sample].  Returns (circuits, params)."""
+    rng = np.random.default_rng([seed, d, n, ord(variant[-1])])
+    _, P = vqa_circuit(d, n, variant, 0, 0)
+    theta = 0.1 * rng.standard_normal(P)
+    enc = rng.uniform(0.0, math.pi, size=(count, n))
+    circuits = []
+    for s in range(count):
+        ops, _ = vqa_circuit(d, n, variant, P + s * n, 0)
+        circuits.append(BatchCircuit(d, n, 2, ops, P))
+    return circuits, np.concatenate([theta, enc.reshape(-1)])

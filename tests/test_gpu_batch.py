@@ -148,3 +148,26 @@ def test_autotuned_batch_matches(tmp_path):
     np.testing.assert_allclose(l1, l0, atol=2e-6)
     np.testing.assert_allclose(g1, g0, atol=2e-5)
     np.testing.assert_allclose(s1, s0, atol=1e-4)
+
+
+@pytest.mark.parametrize("variant", ["R1", "R2", "R3"])
+@pytest.mark.parametrize("d,n", [(3, 4), (10, 2)])
+def test_vqa_batch_vs_oracle(orc, variant, d, n):
+    """Batched VQA training step (Iris-like d=3 n=4, MNIST-like d=10 n=2):
+    complex128 losses and per-sample gradients against the oracle."""
+    qf = gpu_lib()
+    circuits, params = W.vqa_batch(12, d, n, variant)
+    w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
+    b, progs = make_batch(qf, circuits, params, "c128", w0)
+    qf.qf_batch_run(b, params, True)
+    loss, gl, gs = qf.qf_batch_read(b)
+    for i in (0, 5, 11):
+        c = circuits[i]
+        slots, off = qf.qf_batch_circuit_params(b, i)
+        want = orc.grad_bruteforce(c.ops, d, n, params, w0(c), slots=slots)
+        assert np.abs(gl[off:off + len(slots)] - want).max() <= 1e-10
+        wl = orc.loss(orc.run(c.ops, d, n, params=params), d, n, w0(c))
+        assert abs(loss[i] - wl) <= 1e-12
+    qf.qf_batch_free(b)
+    for p in progs:
+        qf.qf_program_free(p)

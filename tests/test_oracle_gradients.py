@@ -61,3 +61,17 @@ def test_shared_and_controlled_parameters(orc):
     w = np.array([0.5, 1.0, -2.0])
     np.testing.assert_allclose(orc.grad_bruteforce(ops, d, n, theta, w),
                                orc.grad_fd(ops, d, n, theta, w), atol=1e-9)
+
+
+@pytest.mark.parametrize("variant", ["R1", "R2", "R3"])
+def test_vqa_variants_bruteforce_vs_fd(orc, variant):
+    """The VQA circuit with each rotation block (RX, RY, level-pair RZ or
+    Gell-Mann RZ, CNOT fan-out): derivative circuits agree with central
+    differences."""
+    d, n = 3, 3
+    ops, P = W.vqa_circuit(d, n, variant, enc_first=0, theta_first=n)
+    params = np.concatenate([np.linspace(0.2, 2.9, n), W.normal_angles(P, seed=P)])
+    w = [1.0] + [0.0] * (n - 1)
+    g = orc.grad_bruteforce(ops, d, n, params, w)
+    fd = orc.grad_fd(ops, d, n, params, w)
+    np.testing.assert_allclose(g, fd, atol=1e-8, rtol=1e-6)
