@@ -60,6 +60,21 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job(ms_local, units_per_rank_step, steps, dist=None, device="cpu"):
+    """(max timed-region ms over ranks, whole-job units/s).  Every rank runs
+    the same per-rank work (weak scaling, independent replicas), so the job
+    processes world x units_per_rank_step per step within the slowest rank's
+    time."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    world = 1
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        world = dist.get_world_size()
+    ms = float(t.item())
+    return ms, units_per_rank_step * steps * world / (ms / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,12 +308,8 @@ def main():
             else:
                 strided_ms += t_
                 strided_bytes += b_
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
     au_step = sum(d ** n for d, n in sizes) * N_GATES
-    value = au_step * args.steps * world / (ms / 1e3)
+    ms, value = whole_job(ms, au_step, args.steps, dist, "cuda")
     launches = sum(pp + 2 for pp in passes) * args.steps
     achieved = (tile_bytes / (tile_ms / 1e3)) / 1e9 if tile_ms > 0 else None
     ratio = traffic_ratio()

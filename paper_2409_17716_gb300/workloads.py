@@ -276,8 +276,10 @@ def vqa_batch(count: int, d: int, n: int, variant: str, seed: int = MASTER_SEED 
     _, P = vqa_circuit(d, n, variant, 0, 0)
     theta = 0.1 * rng.standard_normal(P)
     enc = rng.uniform(0.0, math.pi, size=(count, n))
+    template, _ = vqa_circuit(d, n, variant, 0, 0)   # ops are frozen: shared between samples
     circuits = []
     for s in range(count):
-        ops, _ = vqa_circuit(d, n, variant, P + s * n, 0)
+        ops = list(template)
+        ops[n:2 * n] = [Op("rot", (q,), j=0, k=1, axis="z", param=P + s * n + q) for q in range(n)]
         circuits.append(BatchCircuit(d, n, 2, ops, P))
     return circuits, np.concatenate([theta, enc.reshape(-1)])
