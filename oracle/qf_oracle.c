@@ -20,6 +20,12 @@
  *   row/column number r = sum_i r_i d^(k-1-i), r_i being the level of qudit t_i,
  *   so t_0 is the most significant factor (the left factor of the Kronecker
  *   product).  Matrices are row-major, complex128.
+ *   Registers may mix dimensions (section "Code style": Circuit(dim=[2,3,4])):
+ *   with dims[q] the dimension of qudit q the index is mixed-radix,
+ *   j = sum_q j_q S_q with S_q = prod_{p>q} dims[p], and a k-qudit matrix on
+ *   (t_0..t_{k-1}) has prod_i dims[t_i] rows indexed in the same mixed radix.
+ *   The functions taking a single d are the equal-dimension case of the *_dims
+ *   functions.
  *
  * Arithmetic is IEEE double, compiled with -ffp-contract=off so the x86 and Arm
  * builds round identically.  Gate application is parallelised with OpenMP over
@@ -193,17 +199,25 @@ int or_gate_rot_deriv(int d, int j, int k, double theta, char axis, cplx *dU)
 
 /* Generalised CNOT = SUM ("Generalized CNOT gate"): |c>|t> -> |c>|t + c mod d>,
  * i.e. <c, t (+) c| C_x |c, t> = 1.  The index rule of the paper is used; the
- * displayed case equation there is garbled and is not followed. */
-void or_gate_sum(int d, cplx *U)
+ * displayed case equation there is garbled and is not followed.  With a
+ * control of dimension dc and a target of dimension dt the control level is
+ * added modulo the target's dimension: |c>|t> -> |c>|(t + c) mod dt>
+ * (dc*dt x dc*dt, control = first factor). */
+void or_gate_sum2(int dc, int dt, cplx *U)
 {
-    int D2 = d * d;
+    int D2 = dc * dt;
     for (int a = 0; a < D2 * D2; ++a) U[a] = 0.0;
-    for (int c = 0; c < d; ++c)
-        for (int t = 0; t < d; ++t) {
-            int col = c * d + t;
-            int row = c * d + (t + c) % d;
+    for (int c = 0; c < dc; ++c)
+        for (int t = 0; t < dt; ++t) {
+            int col = c * dt + t;
+            int row = c * dt + (t + c) % dt;
             U[row * D2 + col] = 1.0;
         }
+}
+
+void or_gate_sum(int d, cplx *U)
+{
+    or_gate_sum2(d, d, U);
 }
 
 /* Generalised SWAP ("Generalized SWAP Gate"): |x>|y> -> |y>|x>. */
@@ -216,70 +230,97 @@ void or_gate_swap(int d, cplx *U)
 }
 
 /* Controlled rotation ("Controlled Rotation Gate"):
- *   C = sum_{m=0}^{d-1} |m><m| (x) R^{jk}_alpha(m theta).
- * deriv != 0 returns dC/dtheta = sum_m |m><m| (x) m R'(m theta). */
-static int or_gate_crot_impl(int d, int j, int k, double theta, char axis, int deriv, cplx *U)
+ *   C = sum_{m=0}^{dc-1} |m><m| (x) R^{jk}_alpha(m theta),
+ * control of dimension dc, rotation on a target of dimension dt
+ * (dc*dt x dc*dt).  deriv != 0 returns dC/dtheta = sum_m |m><m| (x) m R'(m theta). */
+static int or_gate_crot_impl(int dc, int dt, int j, int k, double theta, char axis, int deriv, cplx *U)
 {
-    int D2 = d * d;
-    cplx *R = (cplx *)malloc(sizeof(cplx) * (size_t)d * d);
+    int D2 = dc * dt;
+    cplx *R = (cplx *)malloc(sizeof(cplx) * (size_t)dt * dt);
     if (!R) return -1;
     for (int a = 0; a < D2 * D2; ++a) U[a] = 0.0;
-    for (int m = 0; m < d; ++m) {
-        int rc = deriv ? or_gate_rot_deriv(d, j, k, m * theta, axis, R)
-                       : or_gate_rot(d, j, k, m * theta, axis, R);
+    for (int m = 0; m < dc; ++m) {
+        int rc = deriv ? or_gate_rot_deriv(dt, j, k, m * theta, axis, R)
+                       : or_gate_rot(dt, j, k, m * theta, axis, R);
         if (rc != 0) { free(R); return -1; }
-        for (int a = 0; a < d; ++a)
-            for (int b = 0; b < d; ++b) {
-                cplx v = R[a * d + b];
+        for (int a = 0; a < dt; ++a)
+            for (int b = 0; b < dt; ++b) {
+                cplx v = R[a * dt + b];
                 if (deriv) v *= (double)m;
-                U[(m * d + a) * D2 + (m * d + b)] = v;
+                U[(m * dt + a) * D2 + (m * dt + b)] = v;
             }
     }
     free(R);
     return 0;
 }
 
+int or_gate_crot2(int dc, int dt, int j, int k, double theta, char axis, cplx *U)
+{
+    return or_gate_crot_impl(dc, dt, j, k, theta, axis, 0, U);
+}
+
+int or_gate_crot2_deriv(int dc, int dt, int j, int k, double theta, char axis, cplx *U)
+{
+    return or_gate_crot_impl(dc, dt, j, k, theta, axis, 1, U);
+}
+
 int or_gate_crot(int d, int j, int k, double theta, char axis, cplx *U)
 {
-    return or_gate_crot_impl(d, j, k, theta, axis, 0, U);
+    return or_gate_crot_impl(d, d, j, k, theta, axis, 0, U);
 }
 
 int or_gate_crot_deriv(int d, int j, int k, double theta, char axis, cplx *U)
 {
-    return or_gate_crot_impl(d, j, k, theta, axis, 1, U);
+    return or_gate_crot_impl(d, d, j, k, theta, axis, 1, U);
 }
 
 /* ------------------------------------------------------------------------- */
 /* Gate application.                                                          */
 /* ------------------------------------------------------------------------- */
 
-/* Applies the d^k x d^k matrix U to the target qudits of psi (length d^n):
+/* Fills stride[q] = prod_{p>q} dims[p] and returns the state length
+ * prod_q dims[q], or -1 on an invalid dimension. */
+static long long or_strides(const int *dims, int n, long long *stride)
+{
+    long long N = 1;
+    for (int q = n - 1; q >= 0; --q) {
+        if (dims[q] < 2) return -1;
+        stride[q] = N;
+        N *= dims[q];
+    }
+    return N;
+}
+
+/* Applies the K x K matrix U (K = prod_i dims[targets[i]]) to the target
+ * qudits of psi (length prod_q dims[q]):
  *   psi'[.., r, ..] = sum_m U[r, m] psi[.., m, ..]
  * for every assignment of the non-target digits.  Targets must be distinct
  * and in [0, n).  Returns 0, or -1 on invalid arguments. */
-int or_apply(cplx *psi, int d, int n, const int *targets, int k, const cplx *U)
+int or_apply_dims(cplx *psi, const int *dims, int n, const int *targets, int k, const cplx *U)
 {
-    if (d < 2 || n < 1 || k < 1 || k > n) return -1;
+    if (n < 1 || k < 1 || k > n || n > 64) return -1;
     int is_target[64];
-    if (n > 64) return -1;
     memset(is_target, 0, sizeof(is_target));
     for (int i = 0; i < k; ++i) {
         if (targets[i] < 0 || targets[i] >= n || is_target[targets[i]]) return -1;
         is_target[targets[i]] = 1;
     }
-    long long N = or_ipow(d, n);
-    long long K = or_ipow(d, k);
-    long long G = N / K;
     long long *stride = (long long *)malloc(sizeof(long long) * n);
+    if (!stride) return -1;
+    long long N = or_strides(dims, n, stride);
+    if (N < 0) { free(stride); return -1; }
+    long long K = 1;
+    for (int i = 0; i < k; ++i) K *= dims[targets[i]];
+    long long G = N / K;
     long long *off = (long long *)malloc(sizeof(long long) * K);
-    if (!stride || !off) { free(stride); free(off); return -1; }
-    for (int q = 0; q < n; ++q) stride[q] = or_ipow(d, n - 1 - q);
+    if (!off) { free(stride); return -1; }
     /* offset of row/column r inside a group: its digits r_i sit on qudit t_i */
     for (long long r = 0; r < K; ++r) {
         long long rem = r, o = 0;
         for (int i = k - 1; i >= 0; --i) {
-            o += (rem % d) * stride[targets[i]];
-            rem /= d;
+            int dt = dims[targets[i]];
+            o += (rem % dt) * stride[targets[i]];
+            rem /= dt;
         }
         off[r] = o;
     }
@@ -298,8 +339,8 @@ int or_apply(cplx *psi, int d, int n, const int *targets, int k, const cplx *U)
                 long long rem = g, base = 0;
                 for (int q = n - 1; q >= 0; --q) {
                     if (is_target[q]) continue;
-                    base += (rem % d) * stride[q];
-                    rem /= d;
+                    base += (rem % dims[q]) * stride[q];
+                    rem /= dims[q];
                 }
                 for (long long m = 0; m < K; ++m) v[m] = psi[base + off[m]];
                 for (long long r = 0; r < K; ++r) {
@@ -316,6 +357,15 @@ int or_apply(cplx *psi, int d, int n, const int *targets, int k, const cplx *U)
     return fail ? -1 : 0;
 }
 
+/* Equal dimensions: every qudit has dimension d. */
+int or_apply(cplx *psi, int d, int n, const int *targets, int k, const cplx *U)
+{
+    if (d < 2 || n < 1 || n > 64) return -1;
+    int dims[64];
+    for (int q = 0; q < n; ++q) dims[q] = d;
+    return or_apply_dims(psi, dims, n, targets, k, U);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Reductions (serial, plain summation in index order).                      */
 /* ------------------------------------------------------------------------- */
@@ -328,29 +378,39 @@ double or_norm2(const cplx *psi, long long N)
     return s;
 }
 
-/* <N_q> = sum_i i_q |psi_i|^2 for every qudit q, with N = diag(0, 1, ..., d-1)
- * the level-number observable and i_q the q-th digit of i ("Generalized CNOT
- * gate", decimal representation).  out has n entries. */
-void or_expect_number(const cplx *psi, int d, int n, double *out)
+/* <N_q> = sum_i i_q |psi_i|^2 for every qudit q, with N = diag(0, 1, ..., d_q-1)
+ * the level-number observable and i_q the q-th (mixed-radix) digit of i
+ * ("Generalized CNOT gate", decimal representation).  out has n entries. */
+void or_expect_number_dims(const cplx *psi, const int *dims, int n, double *out)
 {
-    long long N = or_ipow(d, n);
+    long long N = 1;
+    for (int q = 0; q < n; ++q) N *= dims[q];
     for (int q = 0; q < n; ++q) out[q] = 0.0;
     for (long long i = 0; i < N; ++i) {
         double p = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
         long long rem = i;
         for (int q = n - 1; q >= 0; --q) {
-            out[q] += (double)(rem % d) * p;
-            rem /= d;
+            out[q] += (double)(rem % dims[q]) * p;
+            rem /= dims[q];
         }
     }
 }
 
-/* <psi| O_q |psi> for a d x d matrix O on qudit q (complex result; real for
- * Hermitian O). */
-void or_expect_obs(const cplx *psi, int d, int n, int q, const cplx *O, double *out_re, double *out_im)
+void or_expect_number(const cplx *psi, int d, int n, double *out)
 {
-    long long N = or_ipow(d, n);
-    long long S = or_ipow(d, n - 1 - q);
+    int dims[64];
+    for (int q = 0; q < n && q < 64; ++q) dims[q] = d;
+    or_expect_number_dims(psi, dims, n, out);
+}
+
+/* <psi| O_q |psi> for a dims[q] x dims[q] matrix O on qudit q (complex
+ * result; real for Hermitian O). */
+void or_expect_obs_dims(const cplx *psi, const int *dims, int n, int q, const cplx *O, double *out_re, double *out_im)
+{
+    long long N = 1, S = 1;
+    for (int p = 0; p < n; ++p) N *= dims[p];
+    for (int p = q + 1; p < n; ++p) S *= dims[p];
+    int d = dims[q];
     cplx acc = 0.0;
     for (long long i = 0; i < N; ++i) {
         long long l = (i / S) % d;
@@ -363,20 +423,40 @@ void or_expect_obs(const cplx *psi, int d, int n, int q, const cplx *O, double *
     *out_im = cimag(acc);
 }
 
+void or_expect_obs(const cplx *psi, int d, int n, int q, const cplx *O, double *out_re, double *out_im)
+{
+    int dims[64];
+    for (int p = 0; p < n && p < 64; ++p) dims[p] = d;
+    or_expect_obs_dims(psi, dims, n, q, O, out_re, out_im);
+}
+
 /* Marginal probabilities of the qudits listed in idx (k of them):
  * out[r] = sum over i whose digits on idx[0..k-1] spell r (idx[0] most
- * significant) of |psi_i|^2.  out has d^k entries. */
-void or_marginal(const cplx *psi, int d, int n, const int *idx, int k, double *out)
+ * significant, mixed radix over dims[idx[a]]) of |psi_i|^2.  out has
+ * prod_a dims[idx[a]] entries. */
+void or_marginal_dims(const cplx *psi, const int *dims, int n, const int *idx, int k, double *out)
 {
-    long long N = or_ipow(d, n);
-    long long K = or_ipow(d, k);
+    long long N = 1, K = 1;
+    long long stride[64];
+    for (int q = n - 1; q >= 0; --q) {
+        stride[q] = N;
+        N *= dims[q];
+    }
+    for (int a = 0; a < k; ++a) K *= dims[idx[a]];
     for (long long r = 0; r < K; ++r) out[r] = 0.0;
     for (long long i = 0; i < N; ++i) {
         double p = creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
         long long r = 0;
-        for (int a = 0; a < k; ++a) r = r * d + (i / or_ipow(d, n - 1 - idx[a])) % d;
+        for (int a = 0; a < k; ++a) r = r * dims[idx[a]] + (i / stride[idx[a]]) % dims[idx[a]];
         out[r] += p;
     }
+}
+
+void or_marginal(const cplx *psi, int d, int n, const int *idx, int k, double *out)
+{
+    int dims[64];
+    for (int q = 0; q < n && q < 64; ++q) dims[q] = d;
+    or_marginal_dims(psi, dims, n, idx, k, out);
 }
 
 /* <a|b> = sum_i conj(a_i) b_i. */

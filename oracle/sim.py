@@ -13,6 +13,11 @@ the circuit runner and the two gradient references:
 
 Ops are read by attribute (kind, qudits, j, k, axis, theta, param, power,
 matrix); the oracle does not import the input generator.
+
+Wherever a function takes ``d`` it also accepts a sequence of per-qudit
+dimensions (mixed-dimension registers, section "Code style":
+``Circuit(dim=[2,3,4])``); the basis index is then mixed-radix with qudit 0
+most significant.
 """
 from __future__ import annotations
 
@@ -36,6 +41,16 @@ def lib():
         L = _c.CDLL(path)
         L.or_apply.argtypes = [_cp, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _cp]
         L.or_apply.restype = _c.c_int
+        L.or_apply_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _cp]
+        L.or_apply_dims.restype = _c.c_int
+        for name in ("or_gate_crot2", "or_gate_crot2_deriv"):
+            f = getattr(L, name)
+            f.argtypes = [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_char, _cp]
+            f.restype = _c.c_int
+        L.or_gate_sum2.argtypes = [_c.c_int, _c.c_int, _cp]
+        L.or_expect_number_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _cp]
+        L.or_expect_obs_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _c.c_int, _cp, _cp, _cp]
+        L.or_marginal_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _cp]
         for name in ("or_gate_rot", "or_gate_rot_deriv", "or_gate_crot", "or_gate_crot_deriv"):
             f = getattr(L, name)
             f.argtypes = [_c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_char, _cp]
@@ -65,6 +80,20 @@ def _ptr(a: np.ndarray):
 
 def _cmat(m: int) -> np.ndarray:
     return np.zeros((m, m), dtype=np.complex128)
+
+
+def dims_of(d, n: int):
+    """Per-qudit dimensions: d repeated n times, or the sequence d itself."""
+    if isinstance(d, (int, np.integer)):
+        return [int(d)] * n
+    dims = [int(x) for x in d]
+    if len(dims) != n:
+        raise ValueError("dims has %d entries for %d qudits" % (len(dims), n))
+    return dims
+
+
+def _ivec(v):
+    return (_c.c_int * len(v))(*[int(x) for x in v])
 
 
 def _chk(rc: int, what: str):
@@ -101,36 +130,48 @@ def rot_deriv(d, j, k, theta, axis):
     U = _cmat(d); _chk(lib().or_gate_rot_deriv(d, j, k, float(theta), axis.encode(), _ptr(U)), "rot_deriv"); return U
 
 
-def sum_gate(d):
-    U = _cmat(d * d); lib().or_gate_sum(d, _ptr(U)); return U
+def sum_gate(d, dt=None):
+    """SUM with control dimension d and target dimension dt (default d)."""
+    dt = d if dt is None else dt
+    U = _cmat(d * dt); lib().or_gate_sum2(d, dt, _ptr(U)); return U
 
 
 def swap_gate(d):
     U = _cmat(d * d); lib().or_gate_swap(d, _ptr(U)); return U
 
 
-def crot(d, j, k, theta, axis):
-    U = _cmat(d * d); _chk(lib().or_gate_crot(d, j, k, float(theta), axis.encode(), _ptr(U)), "crot"); return U
+def crot(d, j, k, theta, axis, dt=None):
+    """Controlled rotation, control dimension d, target dimension dt (default d)."""
+    dt = d if dt is None else dt
+    U = _cmat(d * dt)
+    _chk(lib().or_gate_crot2(d, dt, j, k, float(theta), axis.encode(), _ptr(U)), "crot")
+    return U
 
 
-def crot_deriv(d, j, k, theta, axis):
-    U = _cmat(d * d); _chk(lib().or_gate_crot_deriv(d, j, k, float(theta), axis.encode(), _ptr(U)), "crot_deriv"); return U
+def crot_deriv(d, j, k, theta, axis, dt=None):
+    dt = d if dt is None else dt
+    U = _cmat(d * dt)
+    _chk(lib().or_gate_crot2_deriv(d, dt, j, k, float(theta), axis.encode(), _ptr(U)), "crot_deriv")
+    return U
 
 
 # ---------------------------------------------------------------- states
 def basis(d, n, index=0):
-    psi = np.zeros(d ** n, dtype=np.complex128)
+    psi = np.zeros(int(np.prod(dims_of(d, n), dtype=np.int64)), dtype=np.complex128)
     lib().or_basis_state(_ptr(psi), psi.size, int(index))
     return psi
 
 
-def apply(psi: np.ndarray, d: int, n: int, targets, U: np.ndarray) -> np.ndarray:
+def apply(psi: np.ndarray, d, n: int, targets, U: np.ndarray) -> np.ndarray:
     """In place: psi <- (U on targets) psi."""
-    assert psi.dtype == np.complex128 and psi.flags.c_contiguous and psi.size == d ** n
+    dims = dims_of(d, n)
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous and psi.size == int(np.prod(dims, dtype=np.int64))
     U = np.ascontiguousarray(U, dtype=np.complex128)
-    t = (_c.c_int * len(targets))(*[int(x) for x in targets])
-    assert U.shape == (d ** len(targets),) * 2
-    _chk(lib().or_apply(_ptr(psi), d, n, t, len(targets), _ptr(U)), "apply")
+    if any(not 0 <= int(t) < n for t in targets):
+        raise ValueError("oracle: target qudit out of range")
+    K = int(np.prod([dims[t] for t in targets]))
+    assert U.shape == (K, K)
+    _chk(lib().or_apply_dims(_ptr(psi), _ivec(dims), n, _ivec(targets), len(targets), _ptr(U)), "apply")
     return psi
 
 
@@ -140,21 +181,21 @@ def norm2(psi):
 
 def expect_number(psi, d, n):
     out = np.zeros(n)
-    lib().or_expect_number(_ptr(np.ascontiguousarray(psi)), d, n, _ptr(out))
+    lib().or_expect_number_dims(_ptr(np.ascontiguousarray(psi)), _ivec(dims_of(d, n)), n, _ptr(out))
     return out
 
 
 def expect_obs(psi, d, n, q, O):
     re, im = np.zeros(1), np.zeros(1)
     O = np.ascontiguousarray(O, dtype=np.complex128)
-    lib().or_expect_obs(_ptr(np.ascontiguousarray(psi)), d, n, q, _ptr(O), _ptr(re), _ptr(im))
+    lib().or_expect_obs_dims(_ptr(np.ascontiguousarray(psi)), _ivec(dims_of(d, n)), n, q, _ptr(O), _ptr(re), _ptr(im))
     return complex(re[0], im[0])
 
 
 def marginal(psi, d, n, idx):
-    out = np.zeros(d ** len(idx))
-    t = (_c.c_int * len(idx))(*[int(x) for x in idx])
-    lib().or_marginal(_ptr(np.ascontiguousarray(psi)), d, n, t, len(idx), _ptr(out))
+    dims = dims_of(d, n)
+    out = np.zeros(int(np.prod([dims[q] for q in idx])))
+    lib().or_marginal_dims(_ptr(np.ascontiguousarray(psi)), _ivec(dims), n, _ivec(idx), len(idx), _ptr(out))
     return out
 
 
@@ -165,35 +206,43 @@ def inner(a, b):
 
 
 # ---------------------------------------------------------------- circuits
-def op_matrix(op, d: int, params: Optional[Sequence[float]] = None, deriv: bool = False):
-    """(targets, U) for one op; with deriv=True, (targets, dU/dtheta)."""
+def op_matrix(op, d, params: Optional[Sequence[float]] = None, deriv: bool = False):
+    """(targets, U) for one op; with deriv=True, (targets, dU/dtheta).  d is
+    the register's dimension or its per-qudit dimensions."""
     k = op.kind
     if deriv and k not in ("rot", "crot"):
         raise ValueError("op %s has no angle" % k)
+    if isinstance(d, (int, np.integer)):
+        dq = lambda q: int(d)
+    else:
+        dq = lambda q: int(d[q])
+    t0 = dq(op.qudits[0])
     if k == "h":
-        return op.qudits, fourier(d)
+        return op.qudits, fourier(t0)
     if k == "x":
-        return op.qudits, shift(d, op.power)
+        return op.qudits, shift(t0, op.power)
     if k == "z":
-        return op.qudits, clock(d, op.power)
+        return op.qudits, clock(t0, op.power)
     if k == "rot":
         th = op.angle(params)
         f = rot_deriv if deriv else rot
-        return op.qudits, f(d, op.j, op.k, th, op.axis)
+        return op.qudits, f(t0, op.j, op.k, th, op.axis)
     if k == "crot":
         th = op.angle(params)
         f = crot_deriv if deriv else crot
-        return op.qudits, f(d, op.j, op.k, th, op.axis)
+        return op.qudits, f(t0, op.j, op.k, th, op.axis, dt=dq(op.qudits[1]))
     if k == "sum":
-        return op.qudits, sum_gate(d)
+        return op.qudits, sum_gate(t0, dq(op.qudits[1]))
     if k == "swap":
-        return op.qudits, swap_gate(d)
+        if dq(op.qudits[1]) != t0:
+            raise ValueError("SWAP needs two qudits of the same dimension")
+        return op.qudits, swap_gate(t0)
     if k == "u":
         return op.qudits, np.asarray(op.matrix, dtype=np.complex128)
     raise ValueError("unknown op kind " + k)
 
 
-def run(ops, d: int, n: int, psi: Optional[np.ndarray] = None, params=None) -> np.ndarray:
+def run(ops, d, n: int, psi: Optional[np.ndarray] = None, params=None) -> np.ndarray:
     """Applies ops in order to psi (default |0...0>); returns the final state
     (psi is copied, not modified)."""
     out = basis(d, n, 0) if psi is None else np.array(psi, dtype=np.complex128, copy=True)
@@ -203,13 +252,16 @@ def run(ops, d: int, n: int, psi: Optional[np.ndarray] = None, params=None) -> n
     return out
 
 
-def number_weights_diag(d: int, n: int, weights) -> np.ndarray:
+def number_weights_diag(d, n: int, weights) -> np.ndarray:
     """Diagonal of O = sum_q w_q N_q: entry i is sum_q w_q i_q."""
-    N = d ** n
+    dims = dims_of(d, n)
+    N = int(np.prod(dims, dtype=np.int64))
     i = np.arange(N, dtype=np.int64)
     diag = np.zeros(N)
-    for q in range(n):
-        diag += float(weights[q]) * ((i // d ** (n - 1 - q)) % d)
+    S = 1
+    for q in range(n - 1, -1, -1):
+        diag += float(weights[q]) * ((i // S) % dims[q])
+        S *= dims[q]
     return diag
 
 
@@ -219,7 +271,7 @@ def loss(psi, d, n, weights) -> float:
     return float(np.dot(np.asarray(weights, dtype=float), e))
 
 
-def grad_bruteforce(ops, d: int, n: int, params, weights, psi0=None, slots=None) -> np.ndarray:
+def grad_bruteforce(ops, d, n: int, params, weights, psi0=None, slots=None) -> np.ndarray:
     """dL/dtheta_p for L = sum_q w_q <N_q>, by explicit derivative circuits."""
     params = np.asarray(params, dtype=float)
     P = len(params)
@@ -254,7 +306,7 @@ def grad_bruteforce(ops, d: int, n: int, params, weights, psi0=None, slots=None)
     return g
 
 
-def grad_fd(ops, d: int, n: int, params, weights, h: float = 1e-5, psi0=None, slots=None) -> np.ndarray:
+def grad_fd(ops, d, n: int, params, weights, h: float = 1e-5, psi0=None, slots=None) -> np.ndarray:
     """Central finite differences (L(theta + h e_p) - L(theta - h e_p)) / 2h."""
     params = np.asarray(params, dtype=float)
     slots = range(len(params)) if slots is None else slots

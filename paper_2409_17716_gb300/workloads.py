@@ -32,6 +32,8 @@ Workload recipes (seeded; one master seed, each workload xors in its id):
   * ``vqa_circuit`` / ``vqa_batch`` -- the paper's VQA circuit (Fourier,
     RZ encoding, rotation block R1/R2/R3, CNOT fan-out from qudit 0, rotation
     block) for a batch of samples with uniform stand-in encoding angles.
+  * ``mixed_random_circuit`` / ``mixed_ansatz`` -- circuits on registers that
+    mix qudit dimensions (dims[q] per qudit).
 """
 from __future__ import annotations
 
@@ -283,3 +285,85 @@ def vqa_batch(count: int, d: int, n: int, variant: str, seed: int = MASTER_SEED 
         ops[n:2 * n] = [Op("rot", (q,), j=0, k=1, axis="z", param=P + s * n + q) for q in range(n)]
         circuits.append(BatchCircuit(d, n, 2, ops, P))
     return circuits, np.concatenate([theta, enc.reshape(-1)])
+
+
+MIXED_KINDS = ("u", "rot", "z", "x", "h", "sum", "crot", "swap", "u2")
+
+
+def mixed_random_gate(kind: str, dims: Sequence[int], rng: np.random.Generator,
+                      target: Optional[int] = None) -> Op:
+    """One gate on a register whose qudit q has dimension dims[q]: levels and
+    powers are drawn within the target's dimension; a SWAP needs two qudits of
+    equal dimension (a SUM is drawn when the target has no such partner); a
+    two-qudit Haar U needs d_a * d_b <= 64."""
+    n = len(dims)
+    q = int(rng.integers(n)) if target is None else int(target)
+    d = int(dims[q])
+    if kind == "u":
+        return Op("u", (q,), matrix=haar_unitary(d, rng))
+    if kind == "rot":
+        axis = ("x", "y", "z", "g")[int(rng.integers(4))]
+        if axis == "g":
+            return Op("rot", (q,), j=int(rng.integers(1, d)), axis="g", theta=float(rng.uniform(0.0, TWO_PI)))
+        j, k = _pair(d, rng)
+        return Op("rot", (q,), j=j, k=k, axis=axis, theta=float(rng.uniform(0.0, TWO_PI)))
+    if kind == "z":
+        return Op("z", (q,), power=int(rng.integers(1, d)))
+    if kind == "x":
+        return Op("x", (q,), power=int(rng.integers(1, d)))
+    if kind == "h":
+        return Op("h", (q,))
+    c = int(rng.integers(n - 1))
+    if c >= q:
+        c += 1
+    if kind == "swap":
+        same = [p for p in range(n) if p != q and dims[p] == d]
+        if not same:
+            return Op("sum", (c, q))
+        return Op("swap", (int(same[int(rng.integers(len(same)))]), q))
+    if kind == "sum":
+        return Op("sum", (c, q))
+    if kind == "crot":
+        axis = ("x", "y", "z", "g")[int(rng.integers(4))]
+        if axis == "g":
+            return Op("crot", (c, q), j=int(rng.integers(1, d)), axis="g", theta=float(rng.uniform(0.0, TWO_PI)))
+        j, k = _pair(d, rng)
+        return Op("crot", (c, q), j=j, k=k, axis=axis, theta=float(rng.uniform(0.0, TWO_PI)))
+    if kind == "u2":
+        if dims[c] * d > 64:
+            return Op("sum", (c, q))
+        return Op("u", (c, q), matrix=haar_unitary(int(dims[c]) * d, rng))
+    raise ValueError(kind)
+
+
+def mixed_random_circuit(dims: Sequence[int], n_gates: int = 200, seed: int = MASTER_SEED ^ 7,
+                         kinds: Sequence[str] = MIXED_KINDS) -> List[Op]:
+    """Random sequence on a mixed-dimension register (section "Code style":
+    Circuit(dim=[2,3,4])): kind uniform over `kinds`, then qudits, levels,
+    angle; the seed folds in the dimensions."""
+    rng = np.random.default_rng([seed] + [int(x) for x in dims])
+    return [mixed_random_gate(kinds[int(rng.integers(len(kinds)))], dims, rng) for _ in range(n_gates)]
+
+
+def mixed_ansatz(dims: Sequence[int], layers: int, first_param: int = 0) -> Tuple[List[Op], int]:
+    """Variational layers on a mixed register: Fourier on every qudit (first
+    layer only); per layer RX(0,1), RY(0,1) and Gell-Mann RZ^(d_q - 1) on every
+    qudit, then controlled RY(0,1) from q to q+1 and SUM(q+1, q) for
+    q = 0..n-2.  Parameter slots run layer -> kind -> qudit.  Returns (ops,
+    parameter count)."""
+    n = len(dims)
+    ops: List[Op] = [Op("h", (q,)) for q in range(n)]
+    p = first_param
+    for _ in range(layers):
+        for axis in ("x", "y"):
+            for q in range(n):
+                ops.append(Op("rot", (q,), j=0, k=1, axis=axis, param=p))
+                p += 1
+        for q in range(n):
+            ops.append(Op("rot", (q,), j=int(dims[q]) - 1, axis="g", param=p))
+            p += 1
+        for q in range(n - 1):
+            ops.append(Op("crot", (q, q + 1), j=0, k=1, axis="y", param=p))
+            p += 1
+            ops.append(Op("sum", (q + 1, q)))
+    return ops, p - first_param
