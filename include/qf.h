@@ -87,6 +87,25 @@ qf_status qf_state_init(int d, int n, qf_dtype dt, void *cuda_stream, qf_state *
  * Errors: QF_ERR_ARG (NULL or misaligned pointer, bad sizes). */
 qf_status qf_state_wrap(int d, int n, qf_dtype dt, void *dev_ptr, void *cuda_stream, qf_state **out);
 
+/* Registers that mix qudit dimensions (section "Code style":
+ * Circuit(dim=[2,3,4]) and State('0-1-3', dim=[2,3,4])).  dims[q] in [2, 16]
+ * is the dimension of qudit q; the state holds prod_q dims[q] amplitudes with
+ * the mixed-radix index i = sum_q i_q S_q, S_q = prod_{p>q} dims[p] (qudit 0
+ * most significant).  dims is copied.  Every gate and measurement entry point
+ * accepts such a state: levels and angles are bounded by the target's own
+ * dimension; SUM(c, t) maps |c>|t> to |c>|(t + c) mod d_t> and a controlled
+ * rotation runs over the control's d_c levels; SWAP needs two qudits of equal
+ * dimension; a custom gate's matrix has prod_i dims[targets[i]] (<= 64) rows.
+ * Gates run one launch each (no fusion).  If every entry of dims is equal the
+ * state is an ordinary d^n register.  Limits: prod_q dims[q] / dims[0] < 2^31
+ * (QF_ERR_UNSUPPORTED otherwise).  qf_state_info reports d = 0 for a mixed
+ * register.  Errors as qf_state_init / qf_state_wrap, plus QF_ERR_ARG for
+ * dims NULL or an entry out of range. */
+qf_status qf_state_init_dims(const int *dims, int n, qf_dtype dt, void *cuda_stream, qf_state **out);
+qf_status qf_state_wrap_dims(const int *dims, int n, qf_dtype dt, void *dev_ptr, void *cuda_stream, qf_state **out);
+/* Copies the n per-qudit dimensions into dims[0..n-1] (cap >= n). */
+qf_status qf_state_dims(const qf_state *s, int *dims, int cap);
+
 /* Releases the handle, its scratch buffers and, if owned, the amplitudes.
  * Synchronises the state's stream first.  NULL is accepted. */
 qf_status qf_state_free(qf_state *s);
@@ -206,6 +225,12 @@ qf_status qf_expect_number_noalloc(const void *psi_dev, int d, int n, qf_dtype d
  * (param_slot < 0, angle = theta). */
 
 qf_status qf_program_create(int d, int n, qf_program **out);
+/* A program on a mixed-dimension register (see qf_state_init_dims); it runs on
+ * states of the same dims, one launch per gate, and its adjoint sweep
+ * (qf_program_adjoint / qf_program_gradient) takes one launch per gate that
+ * updates psi and lambda together and adds the gate's gradient term.  Mixed
+ * programs cannot be added to a batch (QF_ERR_UNSUPPORTED). */
+qf_status qf_program_create_dims(const int *dims, int n, qf_program **out);
 qf_status qf_program_free(qf_program *p);
 /* Number of gates recorded, and the number of parameter slots referenced
  * (1 + largest slot, 0 if none). */

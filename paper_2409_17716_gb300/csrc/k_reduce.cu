@@ -275,11 +275,23 @@ cudaError_t launch_expect_number(const Launch &L, const cplx<R> *psi, int d, int
 // kind 0: marginal of qudit q (d outputs); kind 1: <O_q> (re, im); obs_dev
 // holds the d x d FP64 matrix for kind 1.
 template <typename R>
+cudaError_t launch_fibre_reduce_g(const Launch &L, const cplx<R> *psi, int d, long long S, long long N, int kind,
+                                  const double2 *obs_dev, double *partials, double *out_dev);
+
+template <typename R>
 cudaError_t launch_fibre_reduce(const Launch &L, const cplx<R> *psi, int d, int n, int q, int kind, const double2 *obs_dev,
                                 double *partials, double *out_dev) {
     long long S = 1, N = 1;
     for (int i = 0; i < n - 1 - q; ++i) S *= d;
     for (int i = 0; i < n; ++i) N *= d;
+    return launch_fibre_reduce_g<R>(L, psi, d, S, N, kind, obs_dev, partials, out_dev);
+}
+
+// The same on an explicit geometry: target of dimension d at stride S in a
+// state of N amplitudes (mixed registers use the target's own d and S).
+template <typename R>
+cudaError_t launch_fibre_reduce_g(const Launch &L, const cplx<R> *psi, int d, long long S, long long N, int kind,
+                                  const double2 *obs_dev, double *partials, double *out_dev) {
     long long nfib = N / d;
     int maxb = reduce_max_blocks(L.num_sms);
     long long b = (nfib + 255) / 256;
@@ -295,6 +307,10 @@ template cudaError_t launch_fibre_reduce<float>(const Launch &, const cplx<float
                                                 double *, double *);
 template cudaError_t launch_fibre_reduce<double>(const Launch &, const cplx<double> *, int, int, int, int, const double2 *,
                                                  double *, double *);
+template cudaError_t launch_fibre_reduce_g<float>(const Launch &, const cplx<float> *, int, long long, long long, int,
+                                                  const double2 *, double *, double *);
+template cudaError_t launch_fibre_reduce_g<double>(const Launch &, const cplx<double> *, int, long long, long long, int,
+                                                   const double2 *, double *, double *);
 
 }  // namespace qf
 
@@ -422,14 +438,15 @@ namespace qf {
 struct MargArgs {
     int k;                        // measured qudits
     long long stride[kMaxQudits];  // global strides of the measured qudits, most significant first
-    int bins;                     // d^k
+    int dim[kMaxQudits];          // their dimensions
+    int bins;                     // product of their dimensions
 };
 
 // Per-CTA bins in shared memory (FP64 atomics, so the order of additions within
 // a CTA -- and the last bits of a bin -- may vary between runs), one row of
 // partials per CTA, summed in CTA order.
 template <typename R>
-__global__ void __launch_bounds__(256) k_marginal(const cplx<R> *__restrict__ psi, int d, long long N,
+__global__ void __launch_bounds__(256) k_marginal(const cplx<R> *__restrict__ psi, long long N,
                                                    const __grid_constant__ MargArgs M, double *partials) {
     extern __shared__ double bins[];
     for (int b = threadIdx.x; b < M.bins; b += blockDim.x) bins[b] = 0.0;
@@ -438,7 +455,7 @@ __global__ void __launch_bounds__(256) k_marginal(const cplx<R> *__restrict__ ps
         const cplx<R> v = psi[i];
         const double p = (double)v.x * v.x + (double)v.y * v.y;
         int r = 0;
-        for (int a = 0; a < M.k; ++a) r = r * d + (int)((i / M.stride[a]) % d);
+        for (int a = 0; a < M.k; ++a) r = r * M.dim[a] + (int)((i / M.stride[a]) % M.dim[a]);
         atomicAdd(&bins[r], p);
     }
     __syncthreads();
@@ -474,19 +491,20 @@ __global__ void k_cdf(const double *marg, int bins, double *cdf) {
 constexpr int kMargBlocks = 64;
 
 template <typename R>
-cudaError_t launch_marginal(const Launch &L, const cplx<R> *psi, int d, int n, const int *idx, int k, double *partials,
-                            double *out_dev) {
+cudaError_t launch_marginal_dims(const Launch &L, const cplx<R> *psi, const int *dims, int n, const int *idx, int k,
+                                 double *partials, double *out_dev) {
     MargArgs M;
     M.k = k;
     M.bins = 1;
     for (int a = 0; a < k; ++a) {
         long long s = 1;
-        for (int i = 0; i < n - 1 - idx[a]; ++i) s *= d;
+        for (int i = idx[a] + 1; i < n; ++i) s *= dims[i];
         M.stride[a] = s;
-        M.bins *= d;
+        M.dim[a] = dims[idx[a]];
+        M.bins *= dims[idx[a]];
     }
     long long N = 1;
-    for (int i = 0; i < n; ++i) N *= d;
+    for (int i = 0; i < n; ++i) N *= dims[i];
     long long b = (N + 255) / 256;
     int blocks = (int)(b < kMargBlocks ? b : kMargBlocks);
     const size_t smem = (size_t)M.bins * sizeof(double);
@@ -494,9 +512,17 @@ cudaError_t launch_marginal(const Launch &L, const cplx<R> *psi, int d, int n, c
         cudaError_t e = cudaFuncSetAttribute(k_marginal<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_marginal<R><<<blocks, 256, smem, L.stream>>>(psi, d, N, M, partials);
+    k_marginal<R><<<blocks, 256, smem, L.stream>>>(psi, N, M, partials);
     k_sum_partials<<<1, 256, 0, L.stream>>>(partials, blocks, M.bins, out_dev);
     return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_marginal(const Launch &L, const cplx<R> *psi, int d, int n, const int *idx, int k, double *partials,
+                            double *out_dev) {
+    int dims[kMaxQudits];
+    for (int i = 0; i < n; ++i) dims[i] = d;
+    return launch_marginal_dims<R>(L, psi, dims, n, idx, k, partials, out_dev);
 }
 
 int marginal_max_blocks() { return kMargBlocks; }
@@ -518,5 +544,9 @@ template cudaError_t launch_marginal<float>(const Launch &, const cplx<float> *,
                                             double *);
 template cudaError_t launch_marginal<double>(const Launch &, const cplx<double> *, int, int, const int *, int, double *,
                                              double *);
+template cudaError_t launch_marginal_dims<float>(const Launch &, const cplx<float> *, const int *, int, const int *, int,
+                                                 double *, double *);
+template cudaError_t launch_marginal_dims<double>(const Launch &, const cplx<double> *, const int *, int, const int *,
+                                                  int, double *, double *);
 
 }  // namespace qf

@@ -646,6 +646,7 @@ qf_status qf_batch_add(qf_batch *b, const qf_program *p, const double *weights, 
     int d = 0, n = 0;
     qf_status st = program_shape(p, &d, &n);
     if (st != QF_OK) return st;
+    if (d == 0) return set_error(QF_ERR_UNSUPPORTED, "mixed-dimension programs cannot be batched");
     c.d = d;
     c.n = n;
     c.N = ipow_ll(d, n);

@@ -77,6 +77,27 @@ qf_status check_gate(const HGate &g, int d, int n) {
     }
 }
 
+qf_status check_gate_dims(const HGate &g, const int *dims, int n) {
+    auto bad = [&](const std::string &m) { return set_error(QF_ERR_ARG, m); };
+    if (g.nq < 1 || g.nq > 6) return bad("gate needs 1..6 qudits");
+    for (int i = 0; i < g.nq; ++i)
+        if (g.q[i] < 0 || g.q[i] >= n) return bad("qudit index out of range [0, n)");
+    if (g.kind == G_DENSE) {
+        long long K = 1;
+        for (int i = 0; i < g.nq; ++i) K *= dims[g.q[i]];
+        if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: the product of the targets' dims must be <= 64");
+        for (int i = 0; i < g.nq; ++i)
+            for (int k = 0; k < i; ++k)
+                if (g.q[k] == g.q[i]) return bad("qudits of a gate must be distinct");
+        if ((long long)g.U.size() != K * K) return bad("custom gate matrix has the wrong size");
+        return QF_OK;
+    }
+    if (g.kind == G_SWAP && g.nq == 2 && dims[g.q[0]] != dims[g.q[1]])
+        return bad("SWAP needs two qudits of the same dimension");
+    // everything else is bounded by the target's dimension
+    return check_gate(g, dims[gate_target(g)], n);
+}
+
 bool gate_is_param(const HGate &g) { return (g.kind == G_ROT || g.kind == G_CROT) && g.slot >= 0; }
 
 double gate_angle(const HGate &g, const double *params) {
@@ -116,7 +137,8 @@ static void rot_entries(int d, int j, int k, char axis, double th, cd *out, int 
     *mask = msk;
 }
 
-ROp resolve_gate(const HGate &g, int d, double th) {
+// d: the target's dimension; dc: the control's (controlled rotations).
+static ROp resolve_impl(const HGate &g, int d, int dc, double th) {
     ROp r;
     std::memset(&r.op, 0, sizeof(TOp));
     TOp &o = r.op;
@@ -171,8 +193,8 @@ ROp resolve_gate(const HGate &g, int d, double th) {
         o.kind = pair ? OP_CPAIR : OP_CDIAG;
         o.s = g.axis == 'y' ? 1 : 0;       // 1: real 2x2 blocks
         const int per = pair ? 4 : d;
-        r.m.resize((size_t)per * d);
-        for (int m = 0; m < d; ++m) rot_entries(d, g.j, g.k, g.axis, m * th, r.m.data() + per * m, &o.mask);
+        r.m.resize((size_t)per * dc);
+        for (int m = 0; m < dc; ++m) rot_entries(d, g.j, g.k, g.axis, m * th, r.m.data() + per * m, &o.mask);
         break;
     }
     case G_SUM:
@@ -200,6 +222,14 @@ ROp resolve_gate(const HGate &g, int d, double th) {
     return r;
 }
 
+ROp resolve_gate(const HGate &g, int d, double th) { return resolve_impl(g, d, d, th); }
+
+ROp resolve_gate_dims(const HGate &g, const int *dims, double th) {
+    const int t = gate_target(g);
+    const int dc = (g.kind == G_CROT || g.kind == G_SUM) ? dims[g.q[0]] : dims[t];
+    return resolve_impl(g, dims[t], dc, th);
+}
+
 std::vector<cd> dense_of(const ROp &r, int d) {
     std::vector<cd> M((size_t)d * d, cd(0, 0));
     const TOp &o = r.op;
@@ -222,6 +252,66 @@ std::vector<cd> dense_of(const ROp &r, int d) {
         break;
     }
     return M;
+}
+
+// U^+ of a resolved op, in the same op layout.
+ROp dagger(const ROp &r, int d) {
+    ROp o = r;
+    auto cj = [](const cd &z) { return std::conj(z); };
+    switch (r.op.kind) {
+    case OP_DENSE:
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) o.m[a * d + b] = cj(r.m[b * d + a]);
+        break;
+    case OP_PAIR:
+        o.m[0] = cj(r.m[0]); o.m[1] = cj(r.m[2]); o.m[2] = cj(r.m[1]); o.m[3] = cj(r.m[3]);
+        break;
+    case OP_CPAIR:
+        for (size_t m = 0; m < r.m.size() / 4; ++m) {
+            const cd *src = r.m.data() + 4 * m;
+            cd *dst = o.m.data() + 4 * m;
+            dst[0] = cj(src[0]); dst[1] = cj(src[2]); dst[2] = cj(src[1]); dst[3] = cj(src[3]);
+        }
+        break;
+    case OP_DIAG:
+    case OP_CDIAG:
+        for (auto &z : o.m) z = cj(z);
+        break;
+    case OP_SHIFT:
+    case OP_CSHIFT:
+        o.op.s = (d - r.op.s % d) % d;
+        break;
+    case OP_DENSEK: {
+        int K = (int)std::lround(std::sqrt((double)r.m.size()));
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) o.m[a * K + b] = cj(r.m[b * K + a]);
+        break;
+    }
+    default:  // SWAP is its own inverse
+        break;
+    }
+    return o;
+}
+
+// Generator G = S/2 of a parametrised gate (dU/dtheta = -i G U), in the layout
+// of the op's matrix: PAIR kinds (jj, jk, kj, kk), DIAG kinds d real entries.
+std::vector<cd> generator_entries(const HGate &g, int d) {
+    std::vector<cd> G;
+    if (g.axis == 'x') {
+        G = {cd(0, 0), cd(0.5, 0), cd(0.5, 0), cd(0, 0)};
+    } else if (g.axis == 'y') {
+        G = {cd(0, 0), cd(0, -0.5), cd(0, 0.5), cd(0, 0)};
+    } else if (g.axis == 'z') {
+        G.assign(d, cd(0, 0));
+        G[g.j] = cd(0.5, 0);
+        G[g.k] = cd(-0.5, 0);
+    } else {  // 'g'
+        G.assign(d, cd(0, 0));
+        const double gam = std::sqrt(2.0 / ((double)g.j * (double)(g.j + 1)));
+        for (int l = 0; l < g.j; ++l) G[l] = cd(0.5 * gam, 0);
+        G[g.j] = cd(-0.5 * g.j * gam, 0);
+    }
+    return G;
 }
 
 // --------------------------------------------------------------- planning

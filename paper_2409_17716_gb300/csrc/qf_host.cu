@@ -124,9 +124,55 @@ static qf_status run_op_t(qf_state *s, const ROp &r) {
     return QF_OK;
 }
 
+// Mixed-dimension state: strided kinds carry their entries inline; a
+// multi-qudit dense gate's matrix goes through the state's upload staging.
+template <typename R>
+static qf_status run_op_mixed_t(qf_state *s, const ROp &r) {
+    const Launch L = launch_of(s);
+    cplx<R> *psi = reinterpret_cast<cplx<R> *>(s->data);
+    std::vector<cplx<R>> m(r.m.size());
+    for (size_t i = 0; i < r.m.size(); ++i) m[i] = mk<R>((R)r.m[i].real(), (R)r.m[i].imag());
+    const MixedShape shape = mixed_shape(s->dims, s->n);
+    const TOp &o = r.op;
+    const cplx<R> *mat_dev = nullptr;
+    if (!(is_single(o) || is_controlled(o)) && !m.empty()) {
+        const size_t bytes = m.size() * sizeof(cplx<R>);
+        qf_status st = up_reserve(s, bytes);
+        if (st != QF_OK) return st;
+        std::memcpy(s->h_up, m.data(), bytes);
+        st = up_send(s, bytes);
+        if (st != QF_OK) return st;
+        mat_dev = reinterpret_cast<const cplx<R> *>(s->d_up);
+    }
+    if ((is_single(o) || is_controlled(o)) && (int)m.size() > kInlineMat)
+        return set_error(QF_ERR_UNSUPPORTED, "gate table too large for a mixed register");
+    cudaError_t e = mixed_launch<R>(L, psi, shape, o, m.data(), (int)m.size(), mat_dev);
+    if (e != cudaSuccess) return cuda_error(e, "mixed-register gate kernel");
+    return QF_OK;
+}
+
+qf_status run_op_mixed(qf_state *s, const ROp &r) {
+    return s->dt == QF_C64 ? run_op_mixed_t<float>(s, r) : run_op_mixed_t<double>(s, r);
+}
+
+qf_status mixed_expect_number(qf_state *s, double *out_dev) {
+    const Launch L = launch_of(s);
+    const MixedShape shape = mixed_shape(s->dims, s->n);
+    cudaError_t e = s->dt == QF_C64
+                        ? launch_expect_mixed<float>(L, (const float2 *)s->data, shape, s->d_partials, out_dev)
+                        : launch_expect_mixed<double>(L, (const double2 *)s->data, shape, s->d_partials, out_dev);
+    if (e != cudaSuccess) return cuda_error(e, "mixed-register reduction kernels");
+    return QF_OK;
+}
+
 static qf_status apply_gate(qf_state *s, const HGate &g) {
     qf_status st = check_state(s);
     if (st != QF_OK) return st;
+    if (s->mixed) {
+        st = check_gate_dims(g, s->dims, s->n);
+        if (st != QF_OK) return st;
+        return run_op_mixed(s, resolve_gate_dims(g, s->dims, g.theta));
+    }
     st = check_gate(g, s->d, s->n);
     if (st != QF_OK) return st;
     ROp r = resolve_gate(g, s->d, g.theta);
@@ -159,19 +205,33 @@ int qf_expect_size(int d, int n, const qf_obs *obs) {
     }
 }
 
-static qf_status make_state(int d, int n, qf_dtype dt, void *ptr, void *stream, qf_state **out) {
+// dims == nullptr: every qudit has dimension d.
+static qf_status make_state(int d, const int *dims, int n, qf_dtype dt, void *ptr, void *stream, qf_state **out) {
     if (!out) return set_error(QF_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (d < 2 || d > kMaxD) return set_error(QF_ERR_ARG, "d must be in [2, 16]");
-    if (n < 1 || n > kMaxQudits) return set_error(QF_ERR_ARG, "n must be >= 1");
+    if (n < 1 || n > kMaxQudits) return set_error(QF_ERR_ARG, "n must be in [1, 62]");
+    if (dims) {
+        d = dims[0];
+        for (int q = 0; q < n; ++q) {
+            if (dims[q] < 2 || dims[q] > kMaxD) return set_error(QF_ERR_ARG, "every dimension must be in [2, 16]");
+            if (dims[q] != d) d = 0;
+        }
+    } else if (d < 2 || d > kMaxD) {
+        return set_error(QF_ERR_ARG, "d must be in [2, 16]");
+    }
     if (dt != QF_C64 && dt != QF_C128) return set_error(QF_ERR_ARG, "unknown dtype");
-    long double Nf = powl((long double)d, (long double)n);
-    if (Nf > 9.0e15L) return set_error(QF_ERR_ARG, "d^n too large");
+    long double Nf = 1;
+    for (int q = 0; q < n; ++q) Nf *= dims ? dims[q] : d;
+    if (Nf > 9.0e15L) return set_error(QF_ERR_ARG, "state size (product of the dimensions) too large");
+    if (d == 0 && Nf / dims[0] >= 2147483648.0L)
+        return set_error(QF_ERR_UNSUPPORTED, "mixed register: amplitudes / dims[0] must stay below 2^31");
     qf_state *s = new qf_state();
     s->d = d;
     s->n = n;
+    s->mixed = d == 0;
+    for (int q = 0; q < n; ++q) s->dims[q] = dims ? dims[q] : d;
     s->dt = dt;
-    s->N = ipow_ll(d, n);
+    s->N = (long long)Nf;
     s->stream = (cudaStream_t)stream;
     cudaGetDevice(&s->device);
     s->num_sms = device_sms();
@@ -204,7 +264,7 @@ static qf_status make_state(int d, int n, qf_dtype dt, void *ptr, void *stream, 
 }
 
 qf_status qf_state_init(int d, int n, qf_dtype dt, void *cuda_stream, qf_state **out) {
-    qf_status st = make_state(d, n, dt, nullptr, cuda_stream, out);
+    qf_status st = make_state(d, nullptr, n, dt, nullptr, cuda_stream, out);
     if (st != QF_OK) return st;
     st = qf_state_set_basis(*out, 0);
     if (st != QF_OK) {
@@ -216,7 +276,32 @@ qf_status qf_state_init(int d, int n, qf_dtype dt, void *cuda_stream, qf_state *
 
 qf_status qf_state_wrap(int d, int n, qf_dtype dt, void *dev_ptr, void *cuda_stream, qf_state **out) {
     if (!dev_ptr) return set_error(QF_ERR_ARG, "device pointer is NULL");
-    return make_state(d, n, dt, dev_ptr, cuda_stream, out);
+    return make_state(d, nullptr, n, dt, dev_ptr, cuda_stream, out);
+}
+
+qf_status qf_state_init_dims(const int *dims, int n, qf_dtype dt, void *cuda_stream, qf_state **out) {
+    if (!dims) return set_error(QF_ERR_ARG, "dims is NULL");
+    qf_status st = make_state(0, dims, n, dt, nullptr, cuda_stream, out);
+    if (st != QF_OK) return st;
+    st = qf_state_set_basis(*out, 0);
+    if (st != QF_OK) {
+        qf_state_free(*out);
+        *out = nullptr;
+    }
+    return st;
+}
+
+qf_status qf_state_wrap_dims(const int *dims, int n, qf_dtype dt, void *dev_ptr, void *cuda_stream, qf_state **out) {
+    if (!dims) return set_error(QF_ERR_ARG, "dims is NULL");
+    if (!dev_ptr) return set_error(QF_ERR_ARG, "device pointer is NULL");
+    return make_state(0, dims, n, dt, dev_ptr, cuda_stream, out);
+}
+
+qf_status qf_state_dims(const qf_state *s, int *dims, int cap) {
+    if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
+    if (!dims || cap < s->n) return set_error(QF_ERR_ARG, "dims is NULL or shorter than n");
+    for (int q = 0; q < s->n; ++q) dims[q] = s->dims[q];
+    return QF_OK;
 }
 
 qf_status qf_state_free(qf_state *s) {
@@ -268,6 +353,8 @@ qf_status qf_state_set_basis(qf_state *s, long long index) {
 qf_status qf_state_copy(qf_state *dst, const qf_state *src) {
     if (!dst || !src) return set_error(QF_ERR_ARG, "state handle is NULL");
     if (dst->d != src->d || dst->n != src->n || dst->dt != src->dt) return set_error(QF_ERR_ARG, "state shapes differ");
+    for (int q = 0; q < dst->n; ++q)
+        if (dst->dims[q] != src->dims[q]) return set_error(QF_ERR_ARG, "state dimensions differ");
     if (dst == src) return QF_OK;
     const size_t bytes = (size_t)dst->N * (dst->dt == QF_C64 ? 8 : 16);
     QF_CUDA(cudaMemcpyAsync(dst->data, src->data, bytes, cudaMemcpyDeviceToDevice, dst->stream));
@@ -297,8 +384,12 @@ qf_status qf_apply_gate(qf_state *s, const int *targets, int k, const double *U)
     g.kind = G_DENSE;
     g.nq = k;
     for (int i = 0; i < k; ++i) g.q[i] = targets[i];
-    long long K = ipow_ll(s->d, k);
-    if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: d^k must be <= 64");
+    long long K = 1;
+    for (int i = 0; i < k; ++i) {
+        if (targets[i] < 0 || targets[i] >= s->n) return set_error(QF_ERR_ARG, "qudit index out of range [0, n)");
+        K *= s->dims[targets[i]];
+    }
+    if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: the product of the targets' dims must be <= 64");
     g.U.resize((size_t)K * K);
     for (long long i = 0; i < K * K; ++i) g.U[i] = cd(U[2 * i], U[2 * i + 1]);
     return apply_gate(s, g);
@@ -340,6 +431,44 @@ qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev) {
     const Launch L = launch_of(s);
     const bool c64 = s->dt == QF_C64;
     cudaError_t e = cudaSuccess;
+    if (s->mixed) {
+        switch (obs->kind) {
+        case QF_OBS_NUMBER_ALL:
+            return mixed_expect_number(s, out_dev);
+        case QF_OBS_NORM: {
+            qf_status st = mixed_expect_number(s, s->d_out);
+            if (st != QF_OK) return st;
+            QF_CUDA(cudaMemcpyAsync(out_dev, s->d_out + s->n, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+            return QF_OK;
+        }
+        case QF_OBS_MARGINAL:
+        case QF_OBS_HERMITIAN: {
+            if (obs->q < 0 || obs->q >= s->n) return set_error(QF_ERR_ARG, "observable qudit out of range");
+            const int kind = obs->kind == QF_OBS_MARGINAL ? 0 : 1;
+            const int dq = s->dims[obs->q];
+            const double2 *od = nullptr;
+            if (kind == 1) {
+                if (!obs->matrix) return set_error(QF_ERR_ARG, "Hermitian observable needs a matrix");
+                size_t bytes = (size_t)dq * dq * sizeof(double2);
+                qf_status st = up_reserve(s, bytes);
+                if (st != QF_OK) return st;
+                std::memcpy(s->h_up, obs->matrix, bytes);
+                st = up_send(s, bytes);
+                if (st != QF_OK) return st;
+                od = (const double2 *)s->d_up;
+            }
+            const MixedShape shape = mixed_shape(s->dims, s->n);
+            e = c64 ? launch_fibre_reduce_g<float>(L, (const float2 *)s->data, dq, shape.S[obs->q], shape.N, kind, od,
+                                                   s->d_partials, out_dev)
+                    : launch_fibre_reduce_g<double>(L, (const double2 *)s->data, dq, shape.S[obs->q], shape.N, kind, od,
+                                                    s->d_partials, out_dev);
+            if (e != cudaSuccess) return cuda_error(e, "reduction kernels");
+            return QF_OK;
+        }
+        default:
+            return set_error(QF_ERR_ARG, "unknown observable kind");
+        }
+    }
     switch (obs->kind) {
     case QF_OBS_NUMBER_ALL:
         e = c64 ? launch_expect_number<float>(L, (const float2 *)s->data, s->d, s->n, s->d_partials, out_dev)
@@ -389,8 +518,11 @@ qf_status qf_measure(qf_state *s, const int *idx, int k, const double *uniforms,
         for (int b = 0; b < a; ++b)
             if (idx[a] == idx[b]) return set_error(QF_ERR_ARG, "measured qudits must be distinct");
     }
-    long long bins = ipow_ll(s->d, k);
-    if (bins > 16384) return set_error(QF_ERR_UNSUPPORTED, "measure: d^k must be <= 16384");
+    long long bins = 1;
+    for (int a = 0; a < k; ++a) {
+        bins *= s->dims[idx[a]];
+        if (bins > 16384) return set_error(QF_ERR_UNSUPPORTED, "measure: the measured qudits' dims must multiply to <= 16384");
+    }
     if (shots < 0 || (shots > 0 && (!uniforms || !counts))) return set_error(QF_ERR_ARG, "bad shots / uniforms / counts");
     if (!probs) return set_error(QF_ERR_ARG, "probs is NULL");
     const size_t need = (size_t)marginal_max_blocks() * bins * 8 + 2 * bins * 8 + bins * 8 + (size_t)shots * 8 + 256;
@@ -412,8 +544,9 @@ qf_status qf_measure(qf_state *s, const int *idx, int k, const double *uniforms,
     double *u = reinterpret_cast<double *>(cnt + bins);
     const Launch L = launch_of(s);
     if (shots > 0) QF_CUDA(cudaMemcpyAsync(u, uniforms, (size_t)shots * 8, cudaMemcpyHostToDevice, s->stream));
-    cudaError_t e = s->dt == QF_C64 ? launch_marginal<float>(L, (const float2 *)s->data, s->d, s->n, idx, k, part, pr)
-                                    : launch_marginal<double>(L, (const double2 *)s->data, s->d, s->n, idx, k, part, pr);
+    cudaError_t e = s->dt == QF_C64
+                        ? launch_marginal_dims<float>(L, (const float2 *)s->data, s->dims, s->n, idx, k, part, pr)
+                        : launch_marginal_dims<double>(L, (const double2 *)s->data, s->dims, s->n, idx, k, part, pr);
     if (e != cudaSuccess) return cuda_error(e, "marginal kernels");
     if (shots > 0) {
         e = launch_sample(L, pr, (int)bins, cdf, u, shots, cnt);
@@ -428,8 +561,12 @@ qf_status qf_measure(qf_state *s, const int *idx, int k, const double *uniforms,
 qf_status qf_expect(qf_state *s, const qf_obs *obs, double *out_host) {
     if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
     if (!out_host) return set_error(QF_ERR_ARG, "output is NULL");
-    const int cnt = qf_expect_size(s->d, s->n, obs);
+    int cnt = qf_expect_size(s->d, s->n, obs);
     if (cnt < 0) return set_error(QF_ERR_ARG, "unknown observable kind");
+    if (obs->kind == QF_OBS_MARGINAL) {
+        if (obs->q < 0 || obs->q >= s->n) return set_error(QF_ERR_ARG, "observable qudit out of range");
+        cnt = s->dims[obs->q];
+    }
     qf_status st = qf_expect_device(s, obs, s->d_out);
     if (st != QF_OK) return st;
     QF_CUDA(cudaMemcpyAsync(s->h_out, s->d_out, cnt * sizeof(double), cudaMemcpyDeviceToHost, s->stream));

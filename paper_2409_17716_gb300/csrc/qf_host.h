@@ -12,8 +12,59 @@ namespace qf {
 using cd = std::complex<double>;
 
 // ---- kernel launchers (defined next to their kernels)
+// Geometry of a gate on one target: dimension d at stride S with H blocks of
+// d*S amplitudes; for controlled kinds the control's dimension and stride.
+struct StridedGeom {
+    int d = 2;
+    long long S = 1, H = 1;
+    int dc = 2;
+    long long Sc = 1;
+    bool c_above = false;
+};
+StridedGeom uniform_geom(int d, int n, const TOp &op);
 template <typename R>
 cudaError_t launch_strided(const Launch &L, cplx<R> *psi, int d, int n, const TOp &op, const cplx<R> *mat, int nmat);
+template <typename R>
+cudaError_t launch_strided_g(const Launch &L, cplx<R> *psi, const StridedGeom &g, const TOp &op, const cplx<R> *mat,
+                             int nmat);
+long long strided_adj_blocks(const StridedGeom &g);
+template <typename R>
+cudaError_t launch_strided_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, const StridedGeom &g, const TOp &op,
+                               const cplx<R> *mat, int nmat, const cplx<R> *gen, int ngen, double *rows);
+
+// Mixed-radix register: dims[q] per qudit, stride S[q] = prod_{p>q} dims[p].
+struct MixedShape {
+    int n = 0;
+    int dims[kMaxQudits] = {};
+    long long S[kMaxQudits] = {};
+    long long N = 1;
+};
+MixedShape mixed_shape(const int *dims, int n);
+StridedGeom mixed_geom(const MixedShape &m, const TOp &op);
+// Multi-qudit dense gate (matrix on the device, K x K, K = prod of the
+// targets' dims <= kMaxDenseK) or SWAP of two equal-dimension qudits.
+template <typename R>
+cudaError_t launch_group(const Launch &L, cplx<R> *psi, const MixedShape &m, const TOp &op, const cplx<R> *mat_dev);
+template <typename R>
+cudaError_t mixed_launch(const Launch &L, cplx<R> *psi, const MixedShape &m, const TOp &o, const cplx<R> *mat, int nmat,
+                         const cplx<R> *mat_dev);
+template <typename R>
+cudaError_t mixed_adj_launch(const Launch &L, cplx<R> *psi, cplx<R> *lam, const MixedShape &m, const TOp &o,
+                             const cplx<R> *mat, int nmat, const cplx<R> *mat_dev, const cplx<R> *gen, int ngen,
+                             double *rows);
+long long mixed_adj_rows(const MixedShape &m, const TOp &o);
+template <typename R>
+cudaError_t launch_expect_mixed(const Launch &L, const cplx<R> *psi, const MixedShape &m, double *partials,
+                                double *out_dev);
+template <typename R>
+cudaError_t launch_number_obs_mixed(const Launch &L, const cplx<R> *psi, cplx<R> *lam, const MixedShape &m,
+                                    const double *w, double *partials, double *loss_dev);
+template <typename R>
+cudaError_t launch_fibre_reduce_g(const Launch &L, const cplx<R> *psi, int d, long long S, long long N, int kind,
+                                  const double2 *obs_dev, double *partials, double *out_dev);
+template <typename R>
+cudaError_t launch_marginal_dims(const Launch &L, const cplx<R> *psi, const int *dims, int n, const int *idx, int k,
+                                 double *partials, double *out_dev);
 template <typename R>
 cudaError_t launch_tile(const Launch &L, cplx<R> *psi, int d, const TileGeom &g, int nops, const TOp *ops_dev,
                         const cplx<R> *mat_dev, int nmat, const TOp *op_i, const cplx<R> *mat_i,
@@ -68,6 +119,8 @@ struct HGate {
 
 // Validates a gate against (d, n); returns QF_OK or QF_ERR_ARG with message.
 qf_status check_gate(const HGate &g, int d, int n);
+// The same against per-qudit dimensions (levels bounded by the target's d).
+qf_status check_gate_dims(const HGate &g, const int *dims, int n);
 
 // A resolved op: kind (OpKind) on global qudits plus FP64 entries.
 struct ROp {
@@ -77,6 +130,15 @@ struct ROp {
 
 // Entries of a gate at angle theta (theta ignored for fixed gates).
 ROp resolve_gate(const HGate &g, int d, double theta);
+// The same on a mixed register: target and control take their own dims.
+ROp resolve_gate_dims(const HGate &g, const int *dims, double theta);
+// U^+ of a resolved op in the same layout; d = the target's dimension.
+ROp dagger(const ROp &r, int d);
+// Generator G (dU/dtheta = -i G U) of a parametrised gate in the layout of
+// its op: PAIR kinds (jj, jk, kj, kk), DIAG kinds d entries; d = target's dim.
+std::vector<cd> generator_entries(const HGate &g, int d);
+// Target qudit of a gate (the second qudit of crot / sum).
+inline int gate_target(const HGate &g) { return (g.kind == G_CROT || g.kind == G_SUM) ? g.q[1] : g.q[0]; }
 // theta of a gate given the parameter vector.
 double gate_angle(const HGate &g, const double *params);
 // Generator-scaled derivative support: returns false if the gate has no angle.
@@ -123,11 +185,23 @@ TOp localize(const TOp &op, const TileGeom &g, const std::vector<int> &active, i
 qf_status program_shape(const qf_program *p, int *d, int *n);
 qf_status program_gates(const qf_program *p, std::vector<HGate> *out);
 
+// Immediate application of one resolved op on a mixed-dimension state.
+qf_status run_op_mixed(qf_state *s, const ROp &r);
+// Mixed-dimension programs: gate by gate forward, and the per-gate adjoint
+// sweep (loss and gradient to device buffers).
+qf_status mixed_program_run(qf_program *p, qf_state *s, const double *params);
+qf_status mixed_program_adjoint(qf_program *p, qf_state *psi, qf_state *lam, const double *params,
+                                const double *weights, double *loss_dev, double *grad_dev);
+// <N_q> and the norm of a mixed state into out_dev[0..n].
+qf_status mixed_expect_number(qf_state *s, double *out_dev);
+
 }  // namespace qf
 
 // The opaque handle of include/qf.h.
 struct qf_state {
-    int d = 0, n = 0;
+    int d = 0, n = 0;               // d = 0 when the qudits mix dimensions
+    bool mixed = false;
+    int dims[qf::kMaxQudits] = {};  // per-qudit dimensions (all d when uniform)
     qf_dtype dt = QF_C64;
     long long N = 0;
     void *data = nullptr;

@@ -15,7 +15,9 @@
 using namespace qf;
 
 struct qf_program {
-    int d = 0, n = 0;
+    int d = 0, n = 0;                  // d = 0: the qudits mix dimensions
+    bool mixed = false;
+    int dims[kMaxQudits] = {};         // per-qudit dimensions
     std::vector<HGate> gates;
     int num_params = 0;
     bool fuse = true;
@@ -155,66 +157,6 @@ static qf_status upload(qf_program *p, qf_state *s, const std::vector<unsigned c
         p->up_pending = true;
     }
     return QF_OK;
-}
-
-// U^+ of a resolved op, in the same op layout.
-static ROp dagger(const ROp &r, int d) {
-    ROp o = r;
-    auto cj = [](const cd &z) { return std::conj(z); };
-    switch (r.op.kind) {
-    case OP_DENSE:
-        for (int a = 0; a < d; ++a)
-            for (int b = 0; b < d; ++b) o.m[a * d + b] = cj(r.m[b * d + a]);
-        break;
-    case OP_PAIR:
-        o.m[0] = cj(r.m[0]); o.m[1] = cj(r.m[2]); o.m[2] = cj(r.m[1]); o.m[3] = cj(r.m[3]);
-        break;
-    case OP_CPAIR:
-        for (int m = 0; m < d; ++m) {
-            const cd *src = r.m.data() + 4 * m;
-            cd *dst = o.m.data() + 4 * m;
-            dst[0] = cj(src[0]); dst[1] = cj(src[2]); dst[2] = cj(src[1]); dst[3] = cj(src[3]);
-        }
-        break;
-    case OP_DIAG:
-    case OP_CDIAG:
-        for (auto &z : o.m) z = cj(z);
-        break;
-    case OP_SHIFT:
-    case OP_CSHIFT:
-        o.op.s = (d - r.op.s % d) % d;
-        break;
-    case OP_DENSEK: {
-        int K = (int)std::lround(std::sqrt((double)r.m.size()));
-        for (int a = 0; a < K; ++a)
-            for (int b = 0; b < K; ++b) o.m[a * K + b] = cj(r.m[b * K + a]);
-        break;
-    }
-    default:  // SWAP is its own inverse
-        break;
-    }
-    return o;
-}
-
-// Generator G = S/2 of a parametrised gate (dU/dtheta = -i G U), in the layout
-// of the op's matrix: PAIR kinds (jj, jk, kj, kk), DIAG kinds d real entries.
-static std::vector<cd> generator_entries(const HGate &g, int d) {
-    std::vector<cd> G;
-    if (g.axis == 'x') {
-        G = {cd(0, 0), cd(0.5, 0), cd(0.5, 0), cd(0, 0)};
-    } else if (g.axis == 'y') {
-        G = {cd(0, 0), cd(0, -0.5), cd(0, 0.5), cd(0, 0)};
-    } else if (g.axis == 'z') {
-        G.assign(d, cd(0, 0));
-        G[g.j] = cd(0.5, 0);
-        G[g.k] = cd(-0.5, 0);
-    } else {  // 'g'
-        G.assign(d, cd(0, 0));
-        const double gam = std::sqrt(2.0 / ((double)g.j * (double)(g.j + 1)));
-        for (int l = 0; l < g.j; ++l) G[l] = cd(0.5 * gam, 0);
-        G[g.j] = cd(-0.5 * g.j * gam, 0);
-    }
-    return G;
 }
 
 template <typename R>
@@ -459,6 +401,165 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     return QF_OK;
 }
 
+// ---------------------------------------------------------------- mixed registers
+// Programs on registers that mix dimensions run gate by gate: single-qudit and
+// controlled gates through the strided kernel on the target's own (d, S),
+// multi-qudit dense gates and SWAPs through the group kernel.  Matrices of
+// group gates are uploaded with the program's buffer in one copy.
+template <typename R>
+static qf_status mixed_run_t(qf_program *p, qf_state *s, const double *params) {
+    using C = cplx<R>;
+    const MixedShape shape = mixed_shape(p->dims, p->n);
+    std::vector<ROp> ops;
+    std::vector<std::vector<C>> ent;
+    std::vector<size_t> dev_off;
+    std::vector<unsigned char> host;
+    for (const HGate &g : p->gates) {
+        ops.push_back(resolve_gate_dims(g, p->dims, gate_angle(g, params)));
+        const ROp &r = ops.back();
+        std::vector<C> m(r.m.size());
+        for (size_t i = 0; i < r.m.size(); ++i) m[i] = mk<R>((R)r.m[i].real(), (R)r.m[i].imag());
+        size_t off = 0;
+        if (!(is_single(r.op) || is_controlled(r.op)) && !m.empty()) {
+            off = align16(host.size());
+            host.resize(off + m.size() * sizeof(C));
+            std::memcpy(host.data() + off, m.data(), m.size() * sizeof(C));
+        } else if ((int)m.size() > kInlineMat) {
+            return set_error(QF_ERR_UNSUPPORTED, "gate table too large for a mixed register");
+        }
+        ent.push_back(std::move(m));
+        dev_off.push_back(off);
+    }
+    qf_status st = upload(p, s, host);
+    if (st != QF_OK) return st;
+    Launch L;
+    L.stream = s->stream;
+    L.num_sms = s->num_sms;
+    C *psi = reinterpret_cast<C *>(s->data);
+    const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const C *md = reinterpret_cast<const C *>(dev + dev_off[i]);
+        cudaError_t e = mixed_launch<R>(L, psi, shape, ops[i].op, ent[i].data(), (int)ent[i].size(), md);
+        if (e != cudaSuccess) return cuda_error(e, "mixed-register gate kernel");
+    }
+    QF_CUDA(cudaEventRecord(p->done_ev, s->stream));
+    p->ran = true;
+    p->last_passes = (int)ops.size();
+    return QF_OK;
+}
+
+// Adjoint sweep of a mixed-register program: lambda = O psi, then for every
+// gate from the last: gradient term of a parametrised gate and U^+ on psi and
+// lambda in one kernel (k_strided_adj), or U^+ on both through the group
+// kernel; per slot, the terms are summed in a fixed order.
+template <typename R>
+static qf_status mixed_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, const double *params,
+                                 const double *weights, double *loss_dev, double *grad_dev) {
+    using C = cplx<R>;
+    const MixedShape shape = mixed_shape(p->dims, p->n);
+    const int G = (int)p->gates.size();
+    struct Step {
+        ROp r;
+        std::vector<C> m, gen;
+        size_t off = 0;
+        long long rows = 0, nrows = 0;
+    };
+    std::vector<Step> steps(G);
+    std::vector<unsigned char> host;
+    std::vector<std::vector<std::pair<long long, long long>>> terms(p->num_params);
+    long long rows_total = 0;
+    for (int k = 0; k < G; ++k) {
+        const HGate &g = p->gates[G - 1 - k];   // execution order: last gate first
+        Step &st = steps[k];
+        const int dt = p->dims[gate_target(g)];
+        st.r = dagger(resolve_gate_dims(g, p->dims, gate_angle(g, params)), dt);
+        st.m.resize(st.r.m.size());
+        for (size_t i = 0; i < st.r.m.size(); ++i) st.m[i] = mk<R>((R)st.r.m[i].real(), (R)st.r.m[i].imag());
+        const bool strided = is_single(st.r.op) || is_controlled(st.r.op);
+        if (!strided && !st.m.empty()) {
+            st.off = align16(host.size());
+            host.resize(st.off + st.m.size() * sizeof(C));
+            std::memcpy(host.data() + st.off, st.m.data(), st.m.size() * sizeof(C));
+        } else if ((int)st.m.size() > kInlineMat) {
+            return set_error(QF_ERR_UNSUPPORTED, "gate table too large for a mixed register");
+        }
+        if (gate_is_param(g)) {
+            for (const cd &z : generator_entries(g, dt)) st.gen.push_back(mk<R>((R)z.real(), (R)z.imag()));
+            st.nrows = mixed_adj_rows(shape, st.r.op);
+            st.rows = rows_total;
+            rows_total += st.nrows;
+            terms[g.slot].push_back({st.rows, st.nrows});
+        }
+    }
+    // gather table: (base, nrows, ncols = 1, col = 0) per term, slot order
+    const size_t tb = gather_term_bytes();
+    std::vector<int> first(p->num_params + 1, 0);
+    const size_t terms_off = align16(host.size());
+    for (int sl = 0; sl < p->num_params; ++sl) {
+        first[sl + 1] = first[sl] + (int)terms[sl].size();
+        for (auto &t : terms[sl]) {
+            struct {
+                long long base;
+                int nrows, ncols, col, pad;
+            } rec = {t.first, (int)t.second, 1, 0, 0};
+            static_assert(sizeof(rec) == 24, "gather term layout");
+            const size_t at = host.size() < terms_off ? terms_off : host.size();
+            host.resize(at + tb);
+            std::memcpy(host.data() + at, &rec, sizeof(rec));
+        }
+    }
+    const size_t first_off = align16(host.size());
+    host.resize(first_off + first.size() * sizeof(int));
+    std::memcpy(host.data() + first_off, first.data(), first.size() * sizeof(int));
+    if ((size_t)rows_total > p->rows_cap) {
+        if (p->ran) QF_CUDA(cudaEventSynchronize(p->done_ev));
+        if (p->d_rows) cudaFree(p->d_rows);
+        p->d_rows = nullptr;
+        p->rows_cap = 0;
+        size_t cap = (size_t)rows_total + 1024;
+        if (cudaMalloc(&p->d_rows, cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "gradient scratch allocation failed");
+        }
+        p->rows_cap = cap;
+    }
+    qf_status stt = upload(p, psi, host);
+    if (stt != QF_OK) return stt;
+    Launch L;
+    L.stream = psi->stream;
+    L.num_sms = psi->num_sms;
+    C *ps = reinterpret_cast<C *>(psi->data);
+    C *ls = reinterpret_cast<C *>(lam->data);
+    cudaError_t e = launch_number_obs_mixed<R>(L, ps, ls, shape, weights, psi->d_partials, loss_dev);
+    if (e != cudaSuccess) return cuda_error(e, "lambda = O psi");
+    const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
+    for (int k = 0; k < G; ++k) {
+        const Step &st = steps[k];
+        const C *md = reinterpret_cast<const C *>(dev + st.off);
+        e = mixed_adj_launch<R>(L, ps, ls, shape, st.r.op, st.m.data(), (int)st.m.size(), md,
+                                st.gen.empty() ? nullptr : st.gen.data(), (int)st.gen.size(),
+                                st.gen.empty() ? nullptr : p->d_rows + st.rows);
+        if (e != cudaSuccess) return cuda_error(e, "mixed-register adjoint step");
+    }
+    e = launch_grad_gather(L, p->d_rows, dev + terms_off, reinterpret_cast<const int *>(dev + first_off), p->num_params,
+                           grad_dev);
+    if (e != cudaSuccess) return cuda_error(e, "gradient gather");
+    QF_CUDA(cudaEventRecord(p->done_ev, psi->stream));
+    p->ran = true;
+    p->last_passes = G;
+    return QF_OK;
+}
+
+qf_status mixed_program_run(qf_program *p, qf_state *s, const double *params) {
+    return s->dt == QF_C64 ? mixed_run_t<float>(p, s, params) : mixed_run_t<double>(p, s, params);
+}
+
+qf_status mixed_program_adjoint(qf_program *p, qf_state *psi, qf_state *lam, const double *params,
+                                const double *weights, double *loss_dev, double *grad_dev) {
+    return psi->dt == QF_C64 ? mixed_adjoint_t<float>(p, psi, lam, params, weights, loss_dev, grad_dev)
+                             : mixed_adjoint_t<double>(p, psi, lam, params, weights, loss_dev, grad_dev);
+}
+
 qf_status program_shape(const qf_program *p, int *d, int *n) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     *d = p->d;
@@ -483,8 +584,34 @@ qf_status qf_program_create(int d, int n, qf_program **out) {
     qf_program *p = new qf_program();
     p->d = d;
     p->n = n;
+    for (int q = 0; q < n; ++q) p->dims[q] = d;
     *out = p;
     return QF_OK;
+}
+
+qf_status qf_program_create_dims(const int *dims, int n, qf_program **out) {
+    if (!out) return set_error(QF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!dims || n < 1 || n > kMaxQudits) return set_error(QF_ERR_ARG, "dims NULL or n out of range");
+    int d = dims[0];
+    for (int q = 0; q < n; ++q) {
+        if (dims[q] < 2 || dims[q] > kMaxD) return set_error(QF_ERR_ARG, "every dimension must be in [2, 16]");
+        if (dims[q] != d) d = 0;
+    }
+    qf_program *p = new qf_program();
+    p->d = d;
+    p->n = n;
+    p->mixed = d == 0;
+    for (int q = 0; q < n; ++q) p->dims[q] = dims[q];
+    *out = p;
+    return QF_OK;
+}
+
+static bool same_dims(const qf_program *p, const qf_state *s) {
+    if (p->n != s->n || p->d != s->d) return false;
+    for (int q = 0; q < p->n; ++q)
+        if (p->dims[q] != s->dims[q]) return false;
+    return true;
 }
 
 qf_status qf_program_free(qf_program *p) {
@@ -512,7 +639,7 @@ qf_status qf_program_info(const qf_program *p, int *num_gates, int *num_params) 
 
 static qf_status add(qf_program *p, HGate g) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
-    qf_status st = check_gate(g, p->d, p->n);
+    qf_status st = p->mixed ? check_gate_dims(g, p->dims, p->n) : check_gate(g, p->d, p->n);
     if (st != QF_OK) return st;
     if (g.slot >= 0 && g.slot + 1 > p->num_params) p->num_params = g.slot + 1;
     p->gates.push_back(std::move(g));
@@ -527,8 +654,12 @@ qf_status qf_program_add_gate(qf_program *p, const int *targets, int k, const do
     g.kind = G_DENSE;
     g.nq = k;
     for (int i = 0; i < k; ++i) g.q[i] = targets[i];
-    long long K = ipow_ll(p->d, k);
-    if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: d^k must be <= 64");
+    long long K = 1;
+    for (int i = 0; i < k; ++i) {
+        if (targets[i] < 0 || targets[i] >= p->n) return set_error(QF_ERR_ARG, "qudit index out of range [0, n)");
+        K *= p->dims[targets[i]];
+    }
+    if (K > kMaxDenseK) return set_error(QF_ERR_UNSUPPORTED, "custom gate: the product of the targets' dims must be <= 64");
     g.U.resize((size_t)K * K);
     for (long long i = 0; i < K * K; ++i) g.U[i] = cd(U[2 * i], U[2 * i + 1]);
     return add(p, std::move(g));
@@ -596,7 +727,7 @@ qf_status qf_program_set_fusion(qf_program *p, int enable) {
 
 qf_status qf_program_run(qf_program *p, qf_state *s, const double *params) {
     if (!p || !s) return set_error(QF_ERR_ARG, "program or state is NULL");
-    if (p->d != s->d || p->n != s->n) return set_error(QF_ERR_ARG, "program and state sizes differ");
+    if (!same_dims(p, s)) return set_error(QF_ERR_ARG, "program and state sizes differ");
     if (p->num_params > 0 && !params) return set_error(QF_ERR_ARG, "program needs parameters");
     if (p->gates.empty()) {
         p->last_passes = 0;
@@ -609,11 +740,18 @@ qf_status qf_program_run(qf_program *p, qf_state *s, const double *params) {
             return set_error(QF_ERR_CUDA, "event creation failed");
         }
     }
+    if (p->mixed) return mixed_program_run(p, s, params);
     return s->dt == QF_C64 ? run_program_t<float>(p, s, params) : run_program_t<double>(p, s, params);
 }
 
 qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_strided, int *max_ops) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (p->mixed) {   // one launch per gate
+        if (num_passes) *num_passes = (int)p->gates.size();
+        if (num_strided) *num_strided = (int)p->gates.size();
+        if (max_ops) *max_ops = p->gates.empty() ? 0 : 1;
+        return QF_OK;
+    }
     const bool c128 = dt == QF_C128;
     if (!p->plan_valid || p->plan_c128 != c128) {
         p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
@@ -646,13 +784,15 @@ qf_status qf_program_adjoint(qf_program *p, qf_state *psi, qf_state *lam, const 
                              double *loss_dev, double *grad_dev) {
     if (!p || !psi || !lam) return set_error(QF_ERR_ARG, "program or state is NULL");
     if (psi == lam || psi->data == lam->data) return set_error(QF_ERR_ARG, "psi and lambda must be different states");
-    if (p->d != psi->d || p->n != psi->n || lam->d != psi->d || lam->n != psi->n || lam->dt != psi->dt)
+    if (!same_dims(p, psi) || !same_dims(p, lam) || lam->dt != psi->dt)
         return set_error(QF_ERR_ARG, "program and state sizes differ");
     if (!weights) return set_error(QF_ERR_ARG, "weights are NULL");
     if (!loss_dev || !grad_dev) return set_error(QF_ERR_ARG, "outputs are NULL");
     if (p->num_params > 0 && !params) return set_error(QF_ERR_ARG, "program needs parameters");
     qf_status st = ensure_events(p);
     if (st != QF_OK) return st;
+    if (lam->stream != psi->stream) return set_error(QF_ERR_ARG, "psi and lambda must share a stream");
+    if (p->mixed) return mixed_program_adjoint(p, psi, lam, params, weights, loss_dev, grad_dev);
     return psi->dt == QF_C64 ? run_adjoint_t<float>(p, psi, lam, params, weights, loss_dev, grad_dev)
                              : run_adjoint_t<double>(p, psi, lam, params, weights, loss_dev, grad_dev);
 }

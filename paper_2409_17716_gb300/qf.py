@@ -44,6 +44,9 @@ _PROTOS = {
     "qf_expect_size": (_int, [_int, _int, _c.POINTER(qf_obs)]),
     "qf_state_init": (_int, [_int, _int, _int, _vp, _c.POINTER(_vp)]),
     "qf_state_wrap": (_int, [_int, _int, _int, _vp, _vp, _c.POINTER(_vp)]),
+    "qf_state_init_dims": (_int, [_c.POINTER(_int), _int, _int, _vp, _c.POINTER(_vp)]),
+    "qf_state_wrap_dims": (_int, [_c.POINTER(_int), _int, _int, _vp, _vp, _c.POINTER(_vp)]),
+    "qf_state_dims": (_int, [_vp, _c.POINTER(_int), _int]),
     "qf_state_free": (_int, [_vp]),
     "qf_state_ptr": (_int, [_vp, _c.POINTER(_vp), _c.POINTER(_c.c_longlong)]),
     "qf_state_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
@@ -64,6 +67,7 @@ _PROTOS = {
     "qf_measure": (_int, [_vp, _c.POINTER(_int), _int, _c.POINTER(_dbl), _c.c_longlong, _c.POINTER(_dbl),
                           _c.POINTER(_c.c_longlong)]),
     "qf_program_create": (_int, [_int, _int, _c.POINTER(_vp)]),
+    "qf_program_create_dims": (_int, [_c.POINTER(_int), _int, _c.POINTER(_vp)]),
     "qf_program_free": (_int, [_vp]),
     "qf_program_info": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int)]),
     "qf_program_add_gate": (_int, [_vp, _c.POINTER(_int), _int, _c.POINTER(_dbl)]),
@@ -164,6 +168,31 @@ def qf_state_wrap(d: int, n: int, dtype: int, dev_ptr: int, stream=None) -> int:
     return h.value
 
 
+def _ivec(v):
+    return (_int * len(v))(*[int(x) for x in v])
+
+
+def qf_state_init_dims(dims: Sequence[int], dtype: int = QF_C64, stream=None) -> int:
+    """Owned state of a register whose qudit q has dimension dims[q], set to |0...0>."""
+    h = _vp()
+    _call("qf_state_init_dims", _ivec(dims), len(dims), dtype, _stream_ptr(stream), _c.byref(h))
+    return h.value
+
+
+def qf_state_wrap_dims(dims: Sequence[int], dtype: int, dev_ptr: int, stream=None) -> int:
+    h = _vp()
+    _call("qf_state_wrap_dims", _ivec(dims), len(dims), dtype, dev_ptr, _stream_ptr(stream), _c.byref(h))
+    return h.value
+
+
+def qf_state_dims(s: int):
+    """Per-qudit dimensions of a state."""
+    _, n, _ = qf_state_info(s)
+    out = (_int * n)()
+    _call("qf_state_dims", s, out, n)
+    return [out[i] for i in range(n)]
+
+
 def qf_state_free(s: int) -> None:
     _call("qf_state_free", s)
 
@@ -194,7 +223,20 @@ def qf_state_copy(dst: int, src: int) -> None:
 
 
 # ------------------------------------------------------------------ gates
+def _check_matrix(func: str, dims, targets, U) -> None:
+    """The C entry points read prod(dims[t])^2 entries: refuse a matrix of
+    another size before the call."""
+    K = 1
+    for t in targets:
+        if not 0 <= int(t) < len(dims):
+            raise QFError(func, QF_ERR_ARG, "qudit index out of range [0, n)")
+        K *= dims[int(t)]
+    if np.shape(U) != (K, K):
+        raise QFError(func, QF_ERR_ARG, "matrix must be %d x %d for these targets" % (K, K))
+
+
 def qf_apply_gate(s: int, targets: Sequence[int], U) -> None:
+    _check_matrix("qf_apply_gate", qf_state_dims(s), targets, U)
     t = (_int * len(targets))(*[int(x) for x in targets])
     m = _cmatrix(U)
     _call("qf_apply_gate", s, t, len(targets), _dptr(m))
@@ -248,7 +290,10 @@ def qf_expect(s: int, kind: int = QF_OBS_NUMBER_ALL, q: int = 0, matrix=None) ->
     """Host FP64 results (synchronises the state's stream)."""
     o, keep = _obs(kind, q, matrix)
     d, n, _ = qf_state_info(s)
-    out = np.zeros(max(1, lib().qf_expect_size(d, n, _c.byref(o))))
+    size = lib().qf_expect_size(d, n, _c.byref(o))
+    if kind == QF_OBS_MARGINAL and 0 <= q < n:
+        size = qf_state_dims(s)[q]
+    out = np.zeros(max(1, size))
     _call("qf_expect", s, _c.byref(o), _dptr(out))
     del keep
     return out
@@ -264,9 +309,11 @@ def qf_measure(s: int, index: Sequence[int], shots: int = 0, uniforms=None, seed
     """(histogram, probabilities) of the qudits in `index` (the paper's
     measure()).  Shots use `uniforms` if given, else uniforms drawn from a
     seeded numpy generator (input generation, not simulation)."""
-    d, n, _ = qf_state_info(s)
+    dims = qf_state_dims(s)
     k = len(index)
-    bins = d ** k
+    bins = 1
+    for q in index:
+        bins *= dims[int(q)] if 0 <= int(q) < len(dims) else 1
     idx = (_int * k)(*[int(x) for x in index])
     probs = np.zeros(bins)
     counts = np.zeros(bins, dtype=np.int64)
@@ -291,6 +338,12 @@ def qf_program_create(d: int, n: int) -> int:
     return h.value
 
 
+def qf_program_create_dims(dims: Sequence[int]) -> int:
+    h = _vp()
+    _call("qf_program_create_dims", _ivec(dims), len(dims), _c.byref(h))
+    return h.value
+
+
 def qf_program_free(p: int) -> None:
     _call("qf_program_free", p)
 
@@ -301,7 +354,11 @@ def qf_program_info(p: int):
     return g.value, k.value
 
 
-def qf_program_add_gate(p: int, targets: Sequence[int], U) -> None:
+def qf_program_add_gate(p: int, targets: Sequence[int], U, dims: Optional[Sequence[int]] = None) -> None:
+    """Custom gate; with `dims` (the program's per-qudit dimensions) the
+    matrix size is checked before the call."""
+    if dims is not None:
+        _check_matrix("qf_program_add_gate", list(dims), targets, U)
     t = (_int * len(targets))(*[int(x) for x in targets])
     m = _cmatrix(U)
     _call("qf_program_add_gate", p, t, len(targets), _dptr(m))
@@ -471,19 +528,33 @@ def qf_program_plan(p: int, dtype: int = QF_C64):
 # ------------------------------------------------------------------ helpers
 class State:
     """A state whose amplitudes live in a torch tensor (complex64 or
-    complex128) on the current CUDA device, wrapped by a libqf handle."""
+    complex128) on the current CUDA device, wrapped by a libqf handle.  `d`
+    is the qudit dimension, or a sequence of per-qudit dimensions for a
+    register that mixes them (then n = len(d))."""
 
-    def __init__(self, d: int, n: int, dtype: str = "c64", stream=None, tensor=None):
+    def __init__(self, d, n: Optional[int] = None, dtype: str = "c64", stream=None, tensor=None):
         import torch
-        self.d, self.n = d, n
+        mixed = not isinstance(d, (int, np.integer))
+        if mixed:
+            self.dims = [int(x) for x in d]
+            n = len(self.dims) if n is None else n
+            assert n == len(self.dims)
+            self.d = self.dims[0] if len(set(self.dims)) == 1 else 0
+        else:
+            self.dims = [int(d)] * n
+            self.d = int(d)
+        self.n = n
         self.dtype = QF_C64 if dtype in ("c64", "complex64") else QF_C128
         tdt = torch.complex64 if self.dtype == QF_C64 else torch.complex128
-        N = d ** n
+        N = int(np.prod(self.dims, dtype=np.int64))
         if tensor is None:
             tensor = torch.empty(N, dtype=tdt, device="cuda")
         assert tensor.dtype == tdt and tensor.is_cuda and tensor.numel() == N and tensor.is_contiguous()
         self.tensor = tensor
-        self.handle = qf_state_wrap(d, n, self.dtype, tensor.data_ptr(), stream)
+        if mixed:
+            self.handle = qf_state_wrap_dims(self.dims, self.dtype, tensor.data_ptr(), stream)
+        else:
+            self.handle = qf_state_wrap(d, n, self.dtype, tensor.data_ptr(), stream)
 
     def set_basis(self, index: int = 0) -> "State":
         qf_state_set_basis(self.handle, index)
@@ -529,9 +600,11 @@ def apply_ops(s: int, ops: Iterable, params=None) -> None:
             raise ValueError(k)
 
 
-def program_from_ops(d: int, n: int, ops: Iterable, fuse: bool = True) -> int:
-    """Records workload ops into a new program (parameter slots kept)."""
-    p = qf_program_create(d, n)
+def program_from_ops(d, n: int, ops: Iterable, fuse: bool = True) -> int:
+    """Records workload ops into a new program (parameter slots kept); d is
+    the qudit dimension or a sequence of per-qudit dimensions."""
+    p = qf_program_create(d, n) if isinstance(d, (int, np.integer)) else qf_program_create_dims(d)
+    dims = [int(d)] * n if isinstance(d, (int, np.integer)) else [int(x) for x in d]
     for op in ops:
         k = op.kind
         if k == "h":
@@ -549,7 +622,7 @@ def program_from_ops(d: int, n: int, ops: Iterable, fuse: bool = True) -> int:
         elif k == "swap":
             qf_program_add_swap(p, op.qudits[0], op.qudits[1])
         elif k == "u":
-            qf_program_add_gate(p, op.qudits, op.matrix)
+            qf_program_add_gate(p, op.qudits, op.matrix, dims)
         else:
             raise ValueError(k)
     qf_program_set_fusion(p, fuse)
@@ -563,7 +636,7 @@ class Expectation:
     observable weights and runs the adjoint sweep (qf_program_adjoint) on the
     saved output state.  Each forward supports one backward."""
 
-    def __init__(self, d: int, n: int, ops, dtype: str = "c64"):
+    def __init__(self, d, n: int, ops, dtype: str = "c64"):
         self.d, self.n, self.dtype = d, n, dtype
         self.program = program_from_ops(d, n, ops)
         self.num_params = qf_program_info(self.program)[1]

@@ -212,10 +212,15 @@ def batch_circuits(count: int = 4096, seed: int = MASTER_SEED ^ 4,
     return circuits, params
 
 
-def uniform_state(d: int, n: int, seed: int = MASTER_SEED ^ 5) -> np.ndarray:
-    """Random normalised complex128 state of d^n amplitudes (Gaussian entries)."""
-    rng = np.random.default_rng([seed, d, n])
-    N = d ** n
+def uniform_state(d, n: int, seed: int = MASTER_SEED ^ 5) -> np.ndarray:
+    """Random normalised complex128 state of d^n amplitudes (Gaussian
+    entries); d may be a sequence of per-qudit dimensions."""
+    if isinstance(d, (int, np.integer)):
+        rng = np.random.default_rng([seed, d, n])
+        N = d ** n
+    else:
+        rng = np.random.default_rng([seed] + [int(x) for x in d])
+        N = int(np.prod([int(x) for x in d], dtype=np.int64))
     v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
     return (v / np.linalg.norm(v)).astype(np.complex128)
 
