@@ -347,6 +347,8 @@ def main():
         line["batched"] = batch_bench(qf, W, torch)
         torch.cuda.empty_cache()
         line["vqa_training"] = vqa_bench(qf, W, torch)
+        torch.cuda.empty_cache()
+        line["mixed_dims"] = mixed_bench(qf, W, torch, hbm_peak)
     if extras and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -434,6 +436,85 @@ def per_gate_sweep(qf, W, torch, hbm_peak):
                      "median_frac": statistics.median(rows) / hbm_peak,
                      "median_frac_wide": (statistics.median(wide) / hbm_peak) if wide else None}
     st.free()
+    return out
+
+
+def mixed_touched_bytes(op, dims, N, b):
+    """Algorithmic HBM bytes of one gate on a mixed register: read + write of
+    the amplitudes it changes (levels it touches, control level != 0)."""
+    k = op.kind
+    full = 2.0 * N * b
+    if k in ("h", "x") or (k == "u"):
+        return full
+    t = op.qudits[-1]
+    d = dims[t]
+    if k == "z":
+        return full * sum(1 for l in range(d) if (op.power * l) % d) / d
+    if k in ("rot", "crot"):
+        rows = (op.j + 1) if op.axis == "g" else 2
+        f = rows / d
+        if k == "crot":
+            f *= (dims[op.qudits[0]] - 1) / dims[op.qudits[0]]
+        return full * f
+    if k == "sum":
+        return full * (dims[op.qudits[0]] - 1) / dims[op.qudits[0]]
+    if k == "swap":
+        return full * (d * d - d) / (d * d)
+    return full
+
+
+def mixed_bench(qf, W, torch, hbm_peak):
+    """Registers that mix dimensions (dims 2,3,4,5 repeated four times: 16
+    qudits, 2.07e8 amplitudes, 1.66 GB complex64): the random 200-gate
+    sequence, one launch per gate; and the adjoint gradient of a mixed
+    ansatz against 2P + 1 forwards."""
+    import numpy as np
+    dims = [2, 3, 4, 5] * 4
+    n = len(dims)
+    N = int(np.prod(dims))
+    b = 8
+    ops = W.mixed_random_circuit(dims, 200)
+    st = qf.State(dims, n, "c64").set_basis(0)
+    p = qf.program_from_ops(dims, n, ops)
+    qf.qf_program_run(p, st.handle)
+    ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=3)
+    alg = sum(mixed_touched_bytes(op, dims, N, b) for op in ops)
+    out = {"dims": dims, "amps": N, "gates": len(ops), "launches": len(ops), "ms": ms,
+           "au_per_s": N * len(ops) / (ms / 1e3),
+           "algorithmic_gbs": alg / (ms / 1e3) / 1e9, "algorithmic_frac": alg / (ms / 1e3) / 1e9 / hbm_peak,
+           "whole_state_gbs": 2.0 * N * b * len(ops) / (ms / 1e3) / 1e9,
+           "note": "one launch per gate (no fusion on mixed registers); algorithmic bytes count only "
+                   "the levels a gate changes, whole-state bytes 2 N b per gate"}
+    qf.qf_program_free(p)
+    st.free()
+    # adjoint of a mixed ansatz: 16 qudits, 1 layer
+    aops, P = W.mixed_ansatz(dims, 1)
+    theta = W.normal_angles(P, seed=16)
+    w = [1.0] * n
+    p = qf.program_from_ops(dims, n, aops)
+    psi, lam = qf.State(dims, n, "c64"), qf.State(dims, n, "c64")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(P, dtype=torch.float64, device="cuda")
+    ev = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+
+    def fwd():
+        psi.set_basis(0)
+        qf.qf_program_run(p, psi.handle, theta)
+        qf.qf_expect_device(psi.handle, ev.data_ptr(), qf.QF_OBS_NUMBER_ALL)
+
+    def full_grad():
+        psi.set_basis(0)
+        qf.qf_program_run(p, psi.handle, theta)
+        qf.qf_program_adjoint(p, psi.handle, lam.handle, theta, w, loss.data_ptr(), grad.data_ptr())
+
+    full_grad()
+    gms = _time_ms(torch, full_grad, reps=3)
+    fms = _time_ms(torch, fwd, reps=3)
+    out["adjoint"] = {"params": P, "gates": len(aops), "gradient_ms": gms, "forward_ms": fms,
+                      "fd_gradient_ms": (2 * P + 1) * fms, "speedup_vs_fd": (2 * P + 1) * fms / gms}
+    qf.qf_program_free(p)
+    psi.free()
+    lam.free()
     return out
 
 

@@ -48,6 +48,10 @@ def lib():
             f.argtypes = [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_char, _cp]
             f.restype = _c.c_int
         L.or_gate_sum2.argtypes = [_c.c_int, _c.c_int, _cp]
+        L.or_gate_mcx.argtypes = [_c.POINTER(_c.c_int), _c.c_int, _c.c_int, _c.c_int, _cp]
+        L.or_gate_mcx.restype = _c.c_int
+        L.or_gate_mcu.argtypes = [_c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.c_int, _c.c_int, _cp, _cp]
+        L.or_gate_mcu.restype = _c.c_int
         L.or_expect_number_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _cp]
         L.or_expect_obs_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _c.c_int, _cp, _cp, _cp]
         L.or_marginal_dims.argtypes = [_cp, _c.POINTER(_c.c_int), _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _cp]
@@ -155,6 +159,24 @@ def crot_deriv(d, j, k, theta, axis, dt=None):
     return U
 
 
+def mcx_gate(dcs, dt, s=1):
+    """Multi-controlled X^s: target += s * (product of the control levels)."""
+    C = int(np.prod(dcs))
+    U = _cmat(C * dt)
+    _chk(lib().or_gate_mcx(_ivec(dcs), len(dcs), dt, int(s), _ptr(U)), "mcx")
+    return U
+
+
+def mcu_gate(dcs, levels, dt, V):
+    """V on the target when control i is at levels[i] for every i."""
+    C = int(np.prod(dcs))
+    U = _cmat(C * dt)
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    assert V.shape == (dt, dt)
+    _chk(lib().or_gate_mcu(_ivec(dcs), _ivec(levels), len(dcs), dt, _ptr(V), _ptr(U)), "mcu")
+    return U
+
+
 # ---------------------------------------------------------------- states
 def basis(d, n, index=0):
     psi = np.zeros(int(np.prod(dims_of(d, n), dtype=np.int64)), dtype=np.complex128)
@@ -239,6 +261,10 @@ def op_matrix(op, d, params: Optional[Sequence[float]] = None, deriv: bool = Fal
         return op.qudits, swap_gate(t0)
     if k == "u":
         return op.qudits, np.asarray(op.matrix, dtype=np.complex128)
+    if k == "mcx":
+        return op.qudits, mcx_gate([dq(q) for q in op.qudits[:-1]], dq(op.qudits[-1]), op.power)
+    if k == "mcu":
+        return op.qudits, mcu_gate([dq(q) for q in op.qudits[:-1]], op.levels, dq(op.qudits[-1]), op.matrix)
     raise ValueError("unknown op kind " + k)
 
 

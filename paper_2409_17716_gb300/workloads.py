@@ -16,6 +16,8 @@ Gate kinds (paper, Appendix B):
   'sum'  generalised CNOT |c>|t> -> |c>|t + c mod d>
   'swap' generalised SWAP
   'u'    custom d^k x d^k matrix on the listed qudits (first = most significant)
+  'mcx'  multi-controlled X^s on qudits (c_1, .., c_k, t): t += s * c_1 ... c_k
+  'mcu'  d_t x d_t ``matrix`` on the last qudit when control i is at ``levels[i]``
 
 A rotation either carries a fixed angle ``theta`` or names a slot ``param`` of
 a parameter vector supplied at run time.
@@ -58,6 +60,7 @@ class Op:
     param: int = -1
     power: int = 1
     matrix: Optional[np.ndarray] = field(default=None, compare=False, repr=False)
+    levels: Tuple[int, ...] = ()
 
     def angle(self, params: Optional[Sequence[float]] = None) -> float:
         if self.param >= 0:

@@ -183,3 +183,53 @@ def test_mixed_random_circuit_norm(orc):
     assert {op.kind for op in ops} >= {"u", "rot", "z", "x", "h", "sum", "crot", "swap"}
     psi = orc.run(ops, dims, len(dims))
     assert abs(orc.norm2(psi) - 1) < 1e-13
+
+
+def test_toffoli_qubits(orc):
+    """d = 2, two controls: the textbook Toffoli truth table."""
+    U = orc.mcx_gate([2, 2], 2)
+    want = np.eye(8)
+    want[[6, 7]] = want[[7, 6]]
+    assert np.abs(U - want).max() == 0
+    V = np.array([[0, 1], [1, 0]], dtype=complex)
+    assert np.abs(orc.mcu_gate([2, 2], [1, 1], 2, V) - want).max() == 0
+
+
+@pytest.mark.parametrize("dcs,dt", [([3], 3), ([2], 5), ([4], 3)])
+def test_single_control_mcx_is_sum(orc, dcs, dt):
+    assert np.abs(orc.mcx_gate(dcs, dt) - orc.sum_gate(dcs[0], dt)).max() == 0
+
+
+@pytest.mark.parametrize("dcs,dt,s", [([3, 2], 4, 1), ([2, 3, 2], 3, 2), ([4, 4], 2, 1)])
+def test_mcx_structure(orc, dcs, dt, s):
+    """Block diagonal over control assignments with X_dt^(s * product) blocks;
+    the dt-th power is the identity."""
+    U = orc.mcx_gate(dcs, dt, s)
+    X = orc.shift(dt, 1)
+    want = np.zeros_like(U)
+    for c, digs in enumerate(itertools.product(*[range(d) for d in dcs])):
+        blk = np.linalg.matrix_power(X, (s * int(np.prod(digs))) % dt)
+        want[c * dt:(c + 1) * dt, c * dt:(c + 1) * dt] = blk
+    assert np.abs(U - want).max() == 0
+    assert np.abs(np.linalg.matrix_power(U, dt) - np.eye(U.shape[0])).max() == 0
+
+
+def test_mcu_structure(orc):
+    dcs, levels, dt = [3, 2, 4], [2, 1, 0], 3
+    V = W.haar_unitary(dt, np.random.default_rng(8))
+    U = orc.mcu_gate(dcs, levels, dt, V)
+    want = np.zeros_like(U)
+    for c, digs in enumerate(itertools.product(*[range(d) for d in dcs])):
+        want[c * dt:(c + 1) * dt, c * dt:(c + 1) * dt] = V if list(digs) == levels else np.eye(dt)
+    assert np.abs(U - want).max() == 0
+
+
+def test_mc_gates_on_register_vs_full_operator(orc):
+    dims = [3, 2, 4, 3]
+    psi0 = rand_state(int(np.prod(dims)), 9)
+    V = W.haar_unitary(4, np.random.default_rng(2))
+    for op in [W.Op("mcx", (0, 3, 2), power=1), W.Op("mcx", (2, 1, 0, 3), power=2),
+               W.Op("mcu", (3, 0, 2), levels=(2, 1), matrix=V)]:
+        t, U = orc.op_matrix(op, dims)
+        got = orc.apply(psi0.copy(), dims, 4, t, U)
+        assert np.abs(got - full_operator(U, dims, t) @ psi0).max() < 1e-14
