@@ -172,6 +172,23 @@ qf_status qf_apply_z(qf_state *s, int q, int power);
  * H_ab = w^(a b) / sqrt(d). */
 qf_status qf_apply_h(qf_state *s, int q);
 
+/* Multi-controlled gates (section "Quantum Gates" lists a Toffoli and a
+ * multi-controlled NOT gate; the paper gives no qudit definition, so this
+ * library reads them as follows).  controls[0..k-1] (1 <= k <= 5, distinct,
+ * different from target):
+ *   qf_apply_mcx: |c_1..c_k>|t> -> |c_1..c_k>|(t + shift * c_1 c_2 ... c_k) mod d_t>
+ *                 (k = 1 is SUM; d = 2 and shift = 1 is the qubit Toffoli /
+ *                 multi-controlled NOT);
+ *   qf_apply_mcu: the d_t x d_t matrix U (host, row-major, interleaved FP64)
+ *                 on the target where every control c_i is at levels[i]
+ *                 (0 <= levels[i] < d_{c_i}), the identity elsewhere.
+ * One launch, one thread per target fibre; fibres the gate leaves unchanged
+ * are neither read nor written.  Programs run such a gate as a pass of its
+ * own (qf_program_add_mcx / qf_program_add_mcu); batches reject them
+ * (QF_ERR_UNSUPPORTED). */
+qf_status qf_apply_mcx(qf_state *s, const int *controls, int k, int target, int shift);
+qf_status qf_apply_mcu(qf_state *s, const int *controls, const int *levels, int k, int target, const double *U);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Evaluates `obs` (see qf_obs) and writes qf_expect_size() doubles to host
@@ -244,6 +261,8 @@ qf_status qf_program_add_swap(qf_program *p, int a, int b);
 qf_status qf_program_add_x(qf_program *p, int q, int shift);
 qf_status qf_program_add_z(qf_program *p, int q, int power);
 qf_status qf_program_add_h(qf_program *p, int q);
+qf_status qf_program_add_mcx(qf_program *p, const int *controls, int k, int target, int shift);
+qf_status qf_program_add_mcu(qf_program *p, const int *controls, const int *levels, int k, int target, const double *U);
 
 /* Fusion control: enable != 0 (the default) plans fused passes; enable = 0
  * gives one pass per gate, in recorded order (the per-gate kernels).  Takes

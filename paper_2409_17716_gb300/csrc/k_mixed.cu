@@ -127,6 +127,97 @@ cudaError_t launch_group(const Launch &L, cplx<R> *psi, const MixedShape &m, con
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ multi-controlled gates
+// One thread per fibre {hi*(d S) + l*S + lo} of the target (coalesced along lo
+// for S >= 32); the control levels are digits of the fibre's base index.
+// MCSHIFT moves the target by s * (product of the control levels) mod d and
+// skips fibres where that is 0; MCDENSE applies the d x d matrix only where
+// every control sits at its level.
+template <typename R>
+struct MCArgs {
+    int kind, d, nc, s;
+    long long S, nfib;
+    long long cS[6];
+    int cd[6], lv[6];
+    cplx<R> V[kMaxD * kMaxD];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_mc(cplx<R> *__restrict__ psi, const __grid_constant__ MCArgs<R> A) {
+    using C = cplx<R>;
+    const int d = A.d;
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < A.nfib;
+         f += (long long)gridDim.x * blockDim.x) {
+        const long long h = f / A.S, lo = f - h * A.S;
+        const long long base = h * d * A.S + lo;
+        long long prod = 1;
+        bool match = true;
+        for (int i = 0; i < A.nc; ++i) {
+            const int dig = (int)((base / A.cS[i]) % A.cd[i]);
+            prod *= dig;
+            match &= dig == A.lv[i];
+        }
+        C v[kMaxD];
+        if (A.kind == OP_MCSHIFT) {
+            const int sh = (int)(((long long)A.s * (prod % d)) % d);
+            if (sh == 0) continue;
+            for (int m = 0; m < d; ++m) v[m] = psi[base + m * A.S];
+            for (int m = 0; m < d; ++m) {
+                int dst = m + sh;
+                if (dst >= d) dst -= d;
+                psi[base + dst * A.S] = v[m];
+            }
+        } else {
+            if (!match) continue;
+            for (int m = 0; m < d; ++m) v[m] = psi[base + m * A.S];
+            for (int l = 0; l < d; ++l) {
+                C acc = mk<R>(0, 0);
+                for (int m = 0; m < d; ++m) acc = cfma(A.V[l * d + m], v[m], acc);
+                psi[base + l * A.S] = acc;
+            }
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_mc(const Launch &L, cplx<R> *psi, const MixedShape &m, const TOp &op, const cplx<R> *mat, int nmat) {
+    MCArgs<R> A;
+    std::memset(&A, 0, sizeof(A));
+    A.kind = op.kind;
+    A.d = m.dims[op.a];
+    A.S = m.S[op.a];
+    A.nfib = m.N / A.d;
+    A.nc = op.nq;
+    A.s = op.s;
+    if (A.nc < 1 || A.nc > 6 || (op.kind != OP_MCSHIFT && op.kind != OP_MCDENSE)) return cudaErrorInvalidValue;
+    for (int i = 0; i < A.nc; ++i) {
+        A.cS[i] = m.S[op.q[i]];
+        A.cd[i] = m.dims[op.q[i]];
+        A.lv[i] = (op.mask >> (4 * i)) & 15;
+    }
+    if (op.kind == OP_MCDENSE) {
+        if (nmat != A.d * A.d || !mat) return cudaErrorInvalidValue;
+        for (int i = 0; i < nmat; ++i) A.V[i] = mat[i];
+    }
+    long long blocks = (A.nfib + 255) / 256;
+    const long long cap = (long long)L.num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_mc<R><<<(unsigned)blocks, 256, 0, L.stream>>>(psi, A);
+    return cudaGetLastError();
+}
+
+MixedShape uniform_shape(int d, int n) {
+    int dims[kMaxQudits];
+    for (int q = 0; q < n; ++q) dims[q] = d;
+    return mixed_shape(dims, n);
+}
+
+template cudaError_t launch_mc<float>(const Launch &, cplx<float> *, const MixedShape &, const TOp &, const cplx<float> *,
+                                      int);
+template cudaError_t launch_mc<double>(const Launch &, cplx<double> *, const MixedShape &, const TOp &,
+                                       const cplx<double> *, int);
+
 // ------------------------------------------------------------------ row / column reductions
 constexpr int kRowMax = 512;                 // B <= 512: at most 16 columns per lane
 constexpr int kColSlots = kRowMax / 32;
@@ -360,6 +451,7 @@ cudaError_t mixed_launch(const Launch &L, cplx<R> *psi, const MixedShape &m, con
                          const cplx<R> *mat_dev) {
     if ((o.kind == OP_SHIFT && o.s == 0) || (o.kind == OP_DIAG && o.mask == 0)) return cudaSuccess;   // identity
     if (is_single(o) || is_controlled(o)) return launch_strided_g<R>(L, psi, mixed_geom(m, o), o, mat, nmat);
+    if (is_mc(o)) return o.kind == OP_MCSHIFT && o.s == 0 ? cudaSuccess : launch_mc<R>(L, psi, m, o, mat, nmat);
     return launch_group<R>(L, psi, m, o, mat_dev);
 }
 
@@ -372,13 +464,19 @@ cudaError_t mixed_adj_launch(const Launch &L, cplx<R> *psi, cplx<R> *lam, const 
                              double *rows) {
     if (is_single(o) || is_controlled(o))
         return launch_strided_adj<R>(L, psi, lam, mixed_geom(m, o), o, mat, nmat, gen, ngen, rows);
+    if (is_mc(o)) {
+        if (o.kind == OP_MCSHIFT && o.s == 0) return cudaSuccess;
+        cudaError_t e = launch_mc<R>(L, psi, m, o, mat, nmat);
+        if (e != cudaSuccess) return e;
+        return launch_mc<R>(L, lam, m, o, mat, nmat);
+    }
     cudaError_t e = launch_group<R>(L, psi, m, o, mat_dev);
     if (e != cudaSuccess) return e;
     return launch_group<R>(L, lam, m, o, mat_dev);
 }
 
-long long mixed_adj_rows(const MixedShape &m, const TOp &o) {
-    if (is_single(o) || is_controlled(o)) return strided_adj_blocks(mixed_geom(m, o));
+long long mixed_adj_rows(const MixedShape &m, const TOp &o, int num_sms) {
+    if (is_single(o) || is_controlled(o)) return strided_adj_blocks(mixed_geom(m, o), num_sms);
     return 0;
 }
 

@@ -317,92 +317,90 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
     const int d = D > 0 ? D : d_rt;
     const TOp &op = A.op;
     const long long S = A.S;
-    const uint32_t f = blockIdx.x * kStridedBlock + threadIdx.x;
-    bool ok = f < A.nfib;
-    const uint32_t h = A.divS.div(f);
-    const uint32_t lo = f - h * A.S;
-    const long long idx = A.base0 + (long long)h * d * S + lo;
-    const int ctl = control_level<D>(A, h, lo, d);
     C *psi = A.psi, *lam = A.lam;
     double g = 0.0;
-    switch (op.kind) {
-    case OP_DENSE: {
-        if (!ok) break;
-        C v[DM], w[DM];
-#pragma unroll
-        for (int m = 0; m < DM; ++m)
-            if (m < d) { v[m] = psi[idx + m * S]; w[m] = lam[idx + m * S]; }
-#pragma unroll
-        for (int l = 0; l < DM; ++l) {
-            if (l >= d) break;
-            C a = mk<R>(0, 0), b = mk<R>(0, 0);
+    // grid-stride over fibres: the grid is capped so each gate leaves a few
+    // hundred gradient rows, not one per 256 fibres
+    for (uint32_t f = blockIdx.x * kStridedBlock + threadIdx.x; f < A.nfib; f += gridDim.x * kStridedBlock) {
+        const uint32_t h = A.divS.div(f);
+        const uint32_t lo = f - h * A.S;
+        const long long idx = A.base0 + (long long)h * d * S + lo;
+        const int ctl = control_level<D>(A, h, lo, d);
+        switch (op.kind) {
+        case OP_DENSE: {
+            C v[DM], w[DM];
 #pragma unroll
             for (int m = 0; m < DM; ++m)
-                if (m < d) { a = cfma(A.m[l * d + m], v[m], a); b = cfma(A.m[l * d + m], w[m], b); }
-            psi[idx + l * S] = a;
-            lam[idx + l * S] = b;
-        }
-        break;
-    }
-    case OP_PAIR:
-    case OP_CPAIR: {
-        const bool ctrl = op.kind == OP_CPAIR;
-        if (ctrl && ctl == 0) ok = false;
-        if (!ok) break;
-        const C a = psi[idx + op.j * S], b = psi[idx + op.k * S];
-        const C la = lam[idx + op.j * S], lb = lam[idx + op.k * S];
-        if (A.grad) {
-            const C ga = cfma(A.gen[1], b, cmul(A.gen[0], a));
-            const C gb = cfma(A.gen[3], b, cmul(A.gen[2], a));
-            g = (im_conj_mul(la, ga) + im_conj_mul(lb, gb)) * (ctrl ? (double)ctl : 1.0);
-        }
-        const C *M = A.m + (ctrl ? 4 * ctl : 0);
-        psi[idx + op.j * S] = cfma(M[1], b, cmul(M[0], a));
-        psi[idx + op.k * S] = cfma(M[3], b, cmul(M[2], a));
-        lam[idx + op.j * S] = cfma(M[1], lb, cmul(M[0], la));
-        lam[idx + op.k * S] = cfma(M[3], lb, cmul(M[2], la));
-        break;
-    }
-    case OP_DIAG:
-    case OP_CDIAG: {
-        const bool ctrl = op.kind == OP_CDIAG;
-        if (ctrl && ctl == 0) ok = false;
-        if (!ok) break;
-        const C *M = A.m + (ctrl ? d * ctl : 0);
-        double t = 0.0;
+                if (m < d) { v[m] = psi[idx + m * S]; w[m] = lam[idx + m * S]; }
 #pragma unroll
-        for (int l = 0; l < DM; ++l)
-            if (l < d && ((op.mask >> l) & 1)) {
-                const C v = psi[idx + l * S], w = lam[idx + l * S];
-                if (A.grad) t += (double)A.gen[l].x * im_conj_mul(w, v);
-                psi[idx + l * S] = cmul(M[l], v);
-                lam[idx + l * S] = cmul(M[l], w);
+            for (int l = 0; l < DM; ++l) {
+                if (l >= d) break;
+                C a = mk<R>(0, 0), b = mk<R>(0, 0);
+#pragma unroll
+                for (int m = 0; m < DM; ++m)
+                    if (m < d) { a = cfma(A.m[l * d + m], v[m], a); b = cfma(A.m[l * d + m], w[m], b); }
+                psi[idx + l * S] = a;
+                lam[idx + l * S] = b;
             }
-        g = t * (ctrl ? (double)ctl : 1.0);
-        break;
-    }
-    case OP_SHIFT:
-    case OP_CSHIFT: {
-        const bool ctrl = op.kind == OP_CSHIFT;
-        const int sh = ctrl ? (int)((op.s * ctl) % d) : op.s;
-        if (sh == 0) ok = false;
-        if (!ok) break;
-        C v[DM], w[DM];
-#pragma unroll
-        for (int m = 0; m < DM; ++m)
-            if (m < d) { v[m] = psi[idx + m * S]; w[m] = lam[idx + m * S]; }
-#pragma unroll
-        for (int m = 0; m < DM; ++m)
-            if (m < d) {
-                int dst = m + sh;
-                if (dst >= d) dst -= d;
-                psi[idx + dst * S] = v[m];
-                lam[idx + dst * S] = w[m];
+            break;
+        }
+        case OP_PAIR:
+        case OP_CPAIR: {
+            const bool ctrl = op.kind == OP_CPAIR;
+            if (ctrl && ctl == 0) break;
+            const C a = psi[idx + op.j * S], b = psi[idx + op.k * S];
+            const C la = lam[idx + op.j * S], lb = lam[idx + op.k * S];
+            if (A.grad) {
+                const C ga = cfma(A.gen[1], b, cmul(A.gen[0], a));
+                const C gb = cfma(A.gen[3], b, cmul(A.gen[2], a));
+                g += (im_conj_mul(la, ga) + im_conj_mul(lb, gb)) * (ctrl ? (double)ctl : 1.0);
             }
-        break;
-    }
-    default:
-        break;
+            const C *M = A.m + (ctrl ? 4 * ctl : 0);
+            psi[idx + op.j * S] = cfma(M[1], b, cmul(M[0], a));
+            psi[idx + op.k * S] = cfma(M[3], b, cmul(M[2], a));
+            lam[idx + op.j * S] = cfma(M[1], lb, cmul(M[0], la));
+            lam[idx + op.k * S] = cfma(M[3], lb, cmul(M[2], la));
+            break;
+        }
+        case OP_DIAG:
+        case OP_CDIAG: {
+            const bool ctrl = op.kind == OP_CDIAG;
+            if (ctrl && ctl == 0) break;
+            const C *M = A.m + (ctrl ? d * ctl : 0);
+            double t = 0.0;
+#pragma unroll
+            for (int l = 0; l < DM; ++l)
+                if (l < d && ((op.mask >> l) & 1)) {
+                    const C v = psi[idx + l * S], w = lam[idx + l * S];
+                    if (A.grad) t += (double)A.gen[l].x * im_conj_mul(w, v);
+                    psi[idx + l * S] = cmul(M[l], v);
+                    lam[idx + l * S] = cmul(M[l], w);
+                }
+            g += t * (ctrl ? (double)ctl : 1.0);
+            break;
+        }
+        case OP_SHIFT:
+        case OP_CSHIFT: {
+            const bool ctrl = op.kind == OP_CSHIFT;
+            const int sh = ctrl ? (int)((op.s * ctl) % d) : op.s;
+            if (sh == 0) break;
+            C v[DM], w[DM];
+#pragma unroll
+            for (int m = 0; m < DM; ++m)
+                if (m < d) { v[m] = psi[idx + m * S]; w[m] = lam[idx + m * S]; }
+#pragma unroll
+            for (int m = 0; m < DM; ++m)
+                if (m < d) {
+                    int dst = m + sh;
+                    if (dst >= d) dst -= d;
+                    psi[idx + dst * S] = v[m];
+                    lam[idx + dst * S] = w[m];
+                }
+            break;
+        }
+        default:
+            break;
+        }
     }
     if (A.grad) {
         const double s = adj_block_sum(g, red);
@@ -410,15 +408,23 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
     }
 }
 
+constexpr int kAdjBlocksPerSM = 8;
+
+static unsigned adj_grid_of(uint32_t nfib, int num_sms) {
+    long long b = ((long long)nfib + kStridedBlock - 1) / kStridedBlock;
+    const long long cap = (long long)(num_sms > 0 ? num_sms : 1) * kAdjBlocksPerSM;
+    return (unsigned)(b < cap ? b : cap);
+}
+
 // CTAs one adjoint step launches (gradient rows it writes).
-long long strided_adj_blocks(const StridedGeom &g) {
+long long strided_adj_blocks(const StridedGeom &g, int num_sms) {
     const long long max_fib = 1ll << 30;
     long long hper = max_fib / g.S;
     if (hper < 1) hper = 1;
     long long total = 0;
     for (long long h0 = 0; h0 < g.H; h0 += hper) {
         long long nh = g.H - h0 < hper ? g.H - h0 : hper;
-        total += (nh * g.S + kStridedBlock - 1) / kStridedBlock;
+        total += adj_grid_of((uint32_t)(nh * g.S), num_sms);
     }
     return total;
 }
@@ -449,7 +455,7 @@ cudaError_t launch_strided_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, cons
         A.base0 = h0 * d * S;
         A.nfib = (uint32_t)(nh * S);
         A.rows = rows ? rows + row : nullptr;
-        unsigned grid = (unsigned)((A.nfib + kStridedBlock - 1) / kStridedBlock);
+        const unsigned grid = adj_grid_of(A.nfib, L.num_sms);
         row += grid;
         switch (d) {
 #define QF_CASE(DD) case DD: k_strided_adj<R, DD><<<grid, kStridedBlock, 0, L.stream>>>(A, d); break;

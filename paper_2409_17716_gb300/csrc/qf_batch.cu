@@ -653,6 +653,8 @@ qf_status qf_batch_add(qf_batch *b, const qf_program *p, const double *weights, 
     if (c.N > (1ll << 31)) return set_error(QF_ERR_UNSUPPORTED, "batched circuits must have d^n < 2^31");
     st = program_gates(p, &c.gates);
     if (st != QF_OK) return st;
+    for (const HGate &g : c.gates)
+        if (is_mc_gate(g)) return set_error(QF_ERR_UNSUPPORTED, "multi-controlled gates cannot be batched");
     c.w.assign(weights, weights + n);
     if (index) *index = (int)b->circ.size();
     b->amps += c.N;

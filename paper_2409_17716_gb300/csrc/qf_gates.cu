@@ -36,6 +36,20 @@ static cd omega_pow(int d, long long m) {
     return cd(std::cos(a), std::sin(a));
 }
 
+// Multi-controlled gates: 1..5 controls then the target; dq[i] = dimension
+// of g.q[i].
+static qf_status check_mc(const HGate &g, const int *dq) {
+    auto bad = [&](const std::string &m) { return set_error(QF_ERR_ARG, m); };
+    if (g.nq < 2 || g.nq > 6) return bad("multi-controlled gate needs 1..5 controls and a target");
+    const int dt = dq[g.nq - 1];
+    if (g.kind == G_MCU) {
+        for (int i = 0; i + 1 < g.nq; ++i)
+            if (g.lv[i] < 0 || g.lv[i] >= dq[i]) return bad("control level out of range [0, d_c)");
+        if ((int)g.U.size() != dt * dt) return bad("controlled matrix must be d_t x d_t");
+    }
+    return QF_OK;
+}
+
 qf_status check_gate(const HGate &g, int d, int n) {
     auto bad = [&](const std::string &m) { return set_error(QF_ERR_ARG, m); };
     if (g.nq < 1 || g.nq > 6) return bad("gate needs 1..6 qudits");
@@ -72,6 +86,12 @@ qf_status check_gate(const HGate &g, int d, int n) {
     case G_H:
         if (g.nq != 1) return bad("single-qudit gate arity");
         return QF_OK;
+    case G_MCX:
+    case G_MCU: {
+        int dims[6];
+        for (int i = 0; i < 6; ++i) dims[i] = d;
+        return check_mc(g, dims);
+    }
     default:
         return bad("unknown gate kind");
     }
@@ -94,6 +114,14 @@ qf_status check_gate_dims(const HGate &g, const int *dims, int n) {
     }
     if (g.kind == G_SWAP && g.nq == 2 && dims[g.q[0]] != dims[g.q[1]])
         return bad("SWAP needs two qudits of the same dimension");
+    if (is_mc_gate(g)) {
+        for (int i = 0; i < g.nq; ++i)
+            for (int k = 0; k < i; ++k)
+                if (g.q[k] == g.q[i]) return bad("qudits of a gate must be distinct");
+        int dq[6];
+        for (int i = 0; i < g.nq; ++i) dq[i] = dims[g.q[i]];
+        return check_mc(g, dq);
+    }
     // everything else is bounded by the target's dimension
     return check_gate(g, dims[gate_target(g)], n);
 }
@@ -208,6 +236,25 @@ static ROp resolve_impl(const HGate &g, int d, int dc, double th) {
         o.a = g.q[0];
         o.c = g.q[1];
         break;
+    case G_MCX:
+    case G_MCU: {
+        o.a = g.q[g.nq - 1];
+        o.nq = g.nq - 1;
+        for (int i = 0; i < o.nq; ++i) o.q[i] = g.q[i];
+        if (g.kind == G_MCX) {
+            o.kind = OP_MCSHIFT;
+            int sh = g.power % d;
+            if (sh < 0) sh += d;
+            o.s = sh;
+        } else {
+            o.kind = OP_MCDENSE;
+            int msk = 0;
+            for (int i = 0; i < o.nq; ++i) msk |= g.lv[i] << (4 * i);
+            o.mask = msk;
+            r.m = g.U;
+        }
+        break;
+    }
     case G_DENSE:
         if (g.nq == 1) {
             o.kind = OP_DENSE;
@@ -279,7 +326,12 @@ ROp dagger(const ROp &r, int d) {
         break;
     case OP_SHIFT:
     case OP_CSHIFT:
+    case OP_MCSHIFT:
         o.op.s = (d - r.op.s % d) % d;
+        break;
+    case OP_MCDENSE:
+        for (int a = 0; a < d; ++a)
+            for (int b = 0; b < d; ++b) o.m[a * d + b] = cj(r.m[b * d + a]);
         break;
     case OP_DENSEK: {
         int K = (int)std::lround(std::sqrt((double)r.m.size()));
@@ -436,6 +488,13 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
 
     auto finish = [&](std::vector<int> &members, std::vector<bool> &inset) {
         PassPlan p;
+        // a multi-controlled gate runs alone through its own kernel
+        if (members.size() == 1 && is_mc_gate(gates[members[0]])) {
+            p.groups = {{members[0]}};
+            p.mc = true;
+            plan.push_back(p);
+            return;
+        }
         int rL = fit_rl(inset, n, nt_max, rl_min);
         if (rL < 0) rL = fit_rl(inset, n, nt_max, 0);   // a lone wide gate may need SEG < 32
         std::vector<int> active;
@@ -488,7 +547,15 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
             bool take = false;
             // adjoint passes keep at most kMaxGrad gradient columns (register accumulators)
             const bool param_full = for_adjoint && gate_is_param(gates[gi]) && nparam >= kMaxGrad;
-            if (!is_blocked && !param_full && (int)members.size() < op_cap && (fuse || members.empty())) {
+            // a multi-controlled gate is a pass of its own: it starts one, or waits
+            const bool mc = is_mc_gate(gates[gi]);
+            if (mc && !is_blocked && members.empty()) {
+                members.push_back(gi);
+                for (int q : qs) inset[q] = true;
+                ++scan;
+                break;
+            }
+            if (!is_blocked && !param_full && !mc && (int)members.size() < op_cap && (fuse || members.empty())) {
                 std::vector<bool> trial = inset;
                 for (int q : qs) trial[q] = true;
                 if (fit_rl(trial, n, nt_max, rl_min) >= 0) {

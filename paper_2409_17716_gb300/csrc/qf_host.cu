@@ -78,6 +78,12 @@ static qf_status run_op_t(qf_state *s, const ROp &r) {
     for (size_t i = 0; i < r.m.size(); ++i) m[i] = mk<R>((R)r.m[i].real(), (R)r.m[i].imag());
     const TOp &o = r.op;
     if ((o.kind == OP_SHIFT && o.s == 0) || ((o.kind == OP_DIAG) && o.mask == 0)) return QF_OK;  // identity
+    if (is_mc(o)) {
+        if (o.kind == OP_MCSHIFT && o.s == 0) return QF_OK;
+        cudaError_t e = launch_mc<R>(L, psi, uniform_shape(d, n), o, m.data(), (int)m.size());
+        if (e != cudaSuccess) return cuda_error(e, "multi-controlled gate kernel");
+        return QF_OK;
+    }
     const bool single_target = is_single(o) || is_controlled(o);
     const long long S = ipow_ll(d, n - 1 - o.a);
     if (single_target && S >= kWideMin && S < (1ll << 31) && (int)m.size() <= kInlineMat) {
@@ -408,6 +414,41 @@ qf_status qf_apply_crot(qf_state *s, int c, int t, int j, int k, double theta, c
 }
 
 qf_status qf_apply_sum(qf_state *s, int c, int t) { return apply_gate(s, two(G_SUM, c, t)); }
+
+static qf_status mc_hgate(HGate *g, int kind, const int *controls, const int *levels, int k, int target) {
+    if (!controls || k < 1 || k > 5) return set_error(QF_ERR_ARG, "need 1..5 controls");
+    if (kind == G_MCU && !levels) return set_error(QF_ERR_ARG, "levels are NULL");
+    g->kind = kind;
+    g->nq = k + 1;
+    for (int i = 0; i < k; ++i) {
+        g->q[i] = controls[i];
+        g->lv[i] = levels ? levels[i] : 0;
+    }
+    g->q[k] = target;
+    return QF_OK;
+}
+
+qf_status qf_apply_mcx(qf_state *s, const int *controls, int k, int target, int shift) {
+    if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
+    HGate g;
+    qf_status st = mc_hgate(&g, G_MCX, controls, nullptr, k, target);
+    if (st != QF_OK) return st;
+    g.power = shift;
+    return apply_gate(s, g);
+}
+
+qf_status qf_apply_mcu(qf_state *s, const int *controls, const int *levels, int k, int target, const double *U) {
+    if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
+    HGate g;
+    qf_status st = mc_hgate(&g, G_MCU, controls, levels, k, target);
+    if (st != QF_OK) return st;
+    if (!U) return set_error(QF_ERR_ARG, "U is NULL");
+    if (target < 0 || target >= s->n) return set_error(QF_ERR_ARG, "qudit index out of range [0, n)");
+    const int dt = s->dims[target];
+    g.U.resize((size_t)dt * dt);
+    for (int i = 0; i < dt * dt; ++i) g.U[i] = cd(U[2 * i], U[2 * i + 1]);
+    return apply_gate(s, g);
+}
 qf_status qf_apply_swap(qf_state *s, int a, int b) { return apply_gate(s, two(G_SWAP, a, b)); }
 
 qf_status qf_apply_x(qf_state *s, int q, int shift) {

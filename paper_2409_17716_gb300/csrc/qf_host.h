@@ -27,7 +27,7 @@ cudaError_t launch_strided(const Launch &L, cplx<R> *psi, int d, int n, const TO
 template <typename R>
 cudaError_t launch_strided_g(const Launch &L, cplx<R> *psi, const StridedGeom &g, const TOp &op, const cplx<R> *mat,
                              int nmat);
-long long strided_adj_blocks(const StridedGeom &g);
+long long strided_adj_blocks(const StridedGeom &g, int num_sms);
 template <typename R>
 cudaError_t launch_strided_adj(const Launch &L, cplx<R> *psi, cplx<R> *lam, const StridedGeom &g, const TOp &op,
                                const cplx<R> *mat, int nmat, const cplx<R> *gen, int ngen, double *rows);
@@ -52,7 +52,12 @@ template <typename R>
 cudaError_t mixed_adj_launch(const Launch &L, cplx<R> *psi, cplx<R> *lam, const MixedShape &m, const TOp &o,
                              const cplx<R> *mat, int nmat, const cplx<R> *mat_dev, const cplx<R> *gen, int ngen,
                              double *rows);
-long long mixed_adj_rows(const MixedShape &m, const TOp &o);
+long long mixed_adj_rows(const MixedShape &m, const TOp &o, int num_sms);
+// Multi-controlled gate (OP_MCSHIFT / OP_MCDENSE, `mat` = the target's d x d
+// entries rounded to R) on any register shape.
+template <typename R>
+cudaError_t launch_mc(const Launch &L, cplx<R> *psi, const MixedShape &m, const TOp &op, const cplx<R> *mat, int nmat);
+MixedShape uniform_shape(int d, int n);
 template <typename R>
 cudaError_t launch_expect_mixed(const Launch &L, const cplx<R> *psi, const MixedShape &m, double *partials,
                                 double *out_dev);
@@ -103,7 +108,7 @@ qf_status set_error(qf_status s, const std::string &msg);
 qf_status cuda_error(cudaError_t e, const char *where);
 
 // ---- recorded gates (program entries and immediate calls share this form)
-enum GateKind { G_DENSE = 0, G_ROT, G_CROT, G_SUM, G_SWAP, G_X, G_Z, G_H };
+enum GateKind { G_DENSE = 0, G_ROT, G_CROT, G_SUM, G_SWAP, G_X, G_Z, G_H, G_MCX, G_MCU };
 
 struct HGate {
     int kind = G_DENSE;
@@ -113,8 +118,9 @@ struct HGate {
     char axis = 'x';
     int slot = -1;                   // parameter slot, -1 = fixed theta
     double theta = 0.0;
-    int power = 0;                   // X shift / Z power
-    std::vector<cd> U;               // G_DENSE: d^nq x d^nq row-major
+    int power = 0;                   // X shift / Z power / MCX shift
+    int lv[6] = {0, 0, 0, 0, 0, 0};  // G_MCU: control levels
+    std::vector<cd> U;               // G_DENSE: d^nq x d^nq row-major; G_MCU: target d x d
 };
 
 // Validates a gate against (d, n); returns QF_OK or QF_ERR_ARG with message.
@@ -137,8 +143,13 @@ ROp dagger(const ROp &r, int d);
 // Generator G (dU/dtheta = -i G U) of a parametrised gate in the layout of
 // its op: PAIR kinds (jj, jk, kj, kk), DIAG kinds d entries; d = target's dim.
 std::vector<cd> generator_entries(const HGate &g, int d);
-// Target qudit of a gate (the second qudit of crot / sum).
-inline int gate_target(const HGate &g) { return (g.kind == G_CROT || g.kind == G_SUM) ? g.q[1] : g.q[0]; }
+// Target qudit of a gate (the second qudit of crot / sum, the last of a
+// multi-controlled gate).
+inline int gate_target(const HGate &g) {
+    if (g.kind == G_MCX || g.kind == G_MCU) return g.q[g.nq - 1];
+    return (g.kind == G_CROT || g.kind == G_SUM) ? g.q[1] : g.q[0];
+}
+inline bool is_mc_gate(const HGate &g) { return g.kind == G_MCX || g.kind == G_MCU; }
 // theta of a gate given the parameter vector.
 double gate_angle(const HGate &g, const double *params);
 // Generator-scaled derivative support: returns false if the gate has no angle.
@@ -149,6 +160,7 @@ inline bool is_single(const TOp &o) {
     return o.kind == OP_DENSE || o.kind == OP_PAIR || o.kind == OP_DIAG || o.kind == OP_SHIFT;
 }
 inline bool is_controlled(const TOp &o) { return o.kind == OP_CPAIR || o.kind == OP_CDIAG || o.kind == OP_CSHIFT; }
+inline bool is_mc(const TOp &o) { return o.kind == OP_MCSHIFT || o.kind == OP_MCDENSE; }
 
 // d x d matrix of a single-qudit resolved op.
 std::vector<cd> dense_of(const ROp &r, int d);
@@ -156,6 +168,7 @@ std::vector<cd> dense_of(const ROp &r, int d);
 // ---- planning
 struct PassPlan {
     bool strided = false;               // one op through the strided kernel
+    bool mc = false;                    // one multi-controlled gate through its own kernel
     TileGeom geom;                      // tile passes
     std::vector<std::vector<int>> groups;  // per op of the pass: gate indices merged (in order)
     std::vector<int> active;            // active qudits (sorted)

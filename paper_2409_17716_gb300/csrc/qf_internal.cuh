@@ -90,6 +90,8 @@ enum OpKind : int {
     OP_CSHIFT = 6,  // control c level m: shift a by (s * m) mod d        mat: -
     OP_SWAP = 7,    // exchange qudits a and c                          mat: -
     OP_DENSEK = 8,  // d^k x d^k on qudits q[0..k-1] (q[0] most significant) mat: d^(2k)
+    OP_MCSHIFT = 9, // controls q[0..nq-1]: shift a by s * (product of their levels) mod d
+    OP_MCDENSE = 10,// controls q[0..nq-1] at levels (4 bits each in mask): d x d on a   mat: d*d
 };
 
 // One gate, in qudit positions (global for the strided kernel, local tile

@@ -171,7 +171,7 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
     }
     // resolve every pass; tile passes get their op list + pool in one buffer
     struct Built {
-        bool strided;
+        bool strided = false, mc = false;
         ROp rop;
         size_t off = 0;
         int nops = 0, nmat = 0, nstages = 0;
@@ -182,7 +182,8 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         const PassPlan &pp = p->plan[pi];
         Built &b = built[pi];
         b.strided = pp.strided;
-        if (pp.strided) {
+        b.mc = pp.mc;
+        if (pp.strided || pp.mc) {
             b.rop = resolve_group(p->gates, pp.groups[0], d, params);
             continue;
         }
@@ -230,7 +231,17 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         const PassPlan &pp = p->plan[pi];
         const Built &b = built[pi];
         cudaError_t e;
-        if (b.strided) {
+        if (b.mc) {
+            const TOp &o = b.rop.op;
+            if (o.kind == OP_MCSHIFT && o.s == 0) continue;
+            if (p->timing) {
+                p->tkind.push_back(1);
+                p->tbytes.push_back(2.0 * sizeof(C) * (double)N);
+            }
+            std::vector<C> m(b.rop.m.size());
+            for (size_t i = 0; i < m.size(); ++i) m[i] = mk<R>((R)b.rop.m[i].real(), (R)b.rop.m[i].imag());
+            e = launch_mc<R>(L, psi, uniform_shape(d, n), o, m.data(), (int)m.size());
+        } else if (b.strided) {
             const TOp &o = b.rop.op;
             if ((o.kind == OP_SHIFT && o.s == 0) || (o.kind == OP_DIAG && o.mask == 0)) continue;
             if (p->timing) {
@@ -285,6 +296,8 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
         size_t off = 0;
         int nops = 0, nmat = 0, ncols = 0, grid = 0, nstages = 0;
         long long rows_base = 0;
+        bool mc = false;
+        ROp rop;                                // mc passes: U^+
     };
     std::vector<Built> built(np);
     std::vector<unsigned char> host;
@@ -294,6 +307,12 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     for (int k = 0; k < np; ++k) {
         const PassPlan &pp = plan[np - 1 - k];   // execution order: last pass first
         Built &b = built[k];
+        if (pp.mc) {                             // no angle: U^+ on psi and lambda
+            b.mc = true;
+            b.rop = dagger(resolve_group(p->gates, pp.groups[0], d, params), d);
+            b.rows_base = rows_total;
+            continue;
+        }
         std::vector<TOp> ops;
         std::vector<C> pool;
         int ncols = 0;
@@ -382,9 +401,20 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
     cudaError_t e = launch_number_obs<R>(L, ps, ls, d, n, weights, psi->d_partials, loss_dev);
     if (e != cudaSuccess) return cuda_error(e, "lambda = O psi");
     const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
+    const MixedShape ushape = uniform_shape(d, n);
     for (int k = 0; k < np; ++k) {
         const PassPlan &pp = plan[np - 1 - k];
         const Built &b = built[k];
+        if (b.mc) {
+            std::vector<C> m(b.rop.m.size());
+            for (size_t i = 0; i < m.size(); ++i) m[i] = mk<R>((R)b.rop.m[i].real(), (R)b.rop.m[i].imag());
+            if (!(b.rop.op.kind == OP_MCSHIFT && b.rop.op.s == 0)) {
+                e = launch_mc<R>(L, ps, ushape, b.rop.op, m.data(), (int)m.size());
+                if (e == cudaSuccess) e = launch_mc<R>(L, ls, ushape, b.rop.op, m.data(), (int)m.size());
+                if (e != cudaSuccess) return cuda_error(e, "adjoint multi-controlled gate");
+            }
+            continue;
+        }
         const C *pool = reinterpret_cast<const C *>(dev + b.off);
         const TOp *ops = reinterpret_cast<const TOp *>(dev + b.off + align16(b.nmat * sizeof(C)));
         const TStage *stg = b.nstages > 0 ? reinterpret_cast<const TStage *>(ops + b.nops) : nullptr;
@@ -485,7 +515,7 @@ static qf_status mixed_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, co
         }
         if (gate_is_param(g)) {
             for (const cd &z : generator_entries(g, dt)) st.gen.push_back(mk<R>((R)z.real(), (R)z.imag()));
-            st.nrows = mixed_adj_rows(shape, st.r.op);
+            st.nrows = mixed_adj_rows(shape, st.r.op, psi->num_sms);
             st.rows = rows_total;
             rows_total += st.nrows;
             terms[g.slot].push_back({st.rows, st.nrows});
@@ -678,6 +708,40 @@ qf_status qf_program_add_crot(qf_program *p, int c, int t, int j, int k, char ax
     g.kind = G_CROT; g.nq = 2; g.q[0] = c; g.q[1] = t; g.j = j; g.k = k; g.axis = axis;
     g.slot = param_slot < 0 ? -1 : param_slot;
     g.theta = param_slot < 0 ? theta : 0.0;
+    return add(p, g);
+}
+
+static qf_status mc_gate(HGate *g, int kind, const int *controls, const int *levels, int k, int target) {
+    if (!controls || k < 1 || k > 5) return set_error(QF_ERR_ARG, "need 1..5 controls");
+    if (kind == G_MCU && !levels) return set_error(QF_ERR_ARG, "levels are NULL");
+    g->kind = kind;
+    g->nq = k + 1;
+    for (int i = 0; i < k; ++i) {
+        g->q[i] = controls[i];
+        g->lv[i] = levels ? levels[i] : 0;
+    }
+    g->q[k] = target;
+    return QF_OK;
+}
+
+qf_status qf_program_add_mcx(qf_program *p, const int *controls, int k, int target, int shift) {
+    HGate g;
+    qf_status st = mc_gate(&g, G_MCX, controls, nullptr, k, target);
+    if (st != QF_OK) return st;
+    g.power = shift;
+    return add(p, g);
+}
+
+qf_status qf_program_add_mcu(qf_program *p, const int *controls, const int *levels, int k, int target, const double *U) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    HGate g;
+    qf_status st = mc_gate(&g, G_MCU, controls, levels, k, target);
+    if (st != QF_OK) return st;
+    if (!U) return set_error(QF_ERR_ARG, "U is NULL");
+    if (target < 0 || target >= p->n) return set_error(QF_ERR_ARG, "qudit index out of range [0, n)");
+    const int dt = p->dims[target];
+    g.U.resize((size_t)dt * dt);
+    for (int i = 0; i < dt * dt; ++i) g.U[i] = cd(U[2 * i], U[2 * i + 1]);
     return add(p, g);
 }
 

@@ -61,6 +61,8 @@ _PROTOS = {
     "qf_apply_x": (_int, [_vp, _int, _int]),
     "qf_apply_z": (_int, [_vp, _int, _int]),
     "qf_apply_h": (_int, [_vp, _int]),
+    "qf_apply_mcx": (_int, [_vp, _c.POINTER(_int), _int, _int, _int]),
+    "qf_apply_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_expect": (_int, [_vp, _c.POINTER(qf_obs), _c.POINTER(_dbl)]),
     "qf_expect_device": (_int, [_vp, _c.POINTER(qf_obs), _vp]),
     "qf_expect_number_noalloc": (_int, [_vp, _int, _int, _int, _vp, _vp]),
@@ -78,6 +80,8 @@ _PROTOS = {
     "qf_program_add_x": (_int, [_vp, _int, _int]),
     "qf_program_add_z": (_int, [_vp, _int, _int]),
     "qf_program_add_h": (_int, [_vp, _int]),
+    "qf_program_add_mcx": (_int, [_vp, _c.POINTER(_int), _int, _int, _int]),
+    "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
     "qf_program_set_tiling": (_int, [_vp, _int, _int, _int]),
     "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
@@ -270,6 +274,27 @@ def qf_apply_h(s: int, q: int) -> None:
     _call("qf_apply_h", s, q)
 
 
+def qf_apply_mcx(s: int, controls: Sequence[int], target: int, shift: int = 1) -> None:
+    """Target += shift * (product of the control levels) mod d_t."""
+    _call("qf_apply_mcx", s, _ivec(controls), len(controls), int(target), int(shift))
+
+
+def _check_square(func: str, U, dt: int):
+    if np.shape(U) != (dt, dt):
+        raise QFError(func, QF_ERR_ARG, "matrix must be %d x %d for this target" % (dt, dt))
+
+
+def qf_apply_mcu(s: int, controls: Sequence[int], levels: Sequence[int], target: int, U) -> None:
+    """U on the target where control i is at levels[i]."""
+    dims = qf_state_dims(s)
+    if len(levels) != len(controls):
+        raise QFError("qf_apply_mcu", QF_ERR_ARG, "one level per control")
+    if 0 <= int(target) < len(dims):
+        _check_square("qf_apply_mcu", U, dims[int(target)])
+    m = _cmatrix(U)
+    _call("qf_apply_mcu", s, _ivec(controls), _ivec(levels), len(controls), int(target), _dptr(m))
+
+
 # ------------------------------------------------------------------ measurement
 def _obs(kind: int, q: int = 0, matrix=None):
     o = qf_obs()
@@ -391,6 +416,20 @@ def qf_program_add_z(p: int, q: int, power: int = 1) -> None:
 
 def qf_program_add_h(p: int, q: int) -> None:
     _call("qf_program_add_h", p, q)
+
+
+def qf_program_add_mcx(p: int, controls: Sequence[int], target: int, shift: int = 1) -> None:
+    _call("qf_program_add_mcx", p, _ivec(controls), len(controls), int(target), int(shift))
+
+
+def qf_program_add_mcu(p: int, controls: Sequence[int], levels: Sequence[int], target: int, U,
+                       dims: Optional[Sequence[int]] = None) -> None:
+    if len(levels) != len(controls):
+        raise QFError("qf_program_add_mcu", QF_ERR_ARG, "one level per control")
+    if dims is not None and 0 <= int(target) < len(dims):
+        _check_square("qf_program_add_mcu", U, int(dims[int(target)]))
+    m = _cmatrix(U)
+    _call("qf_program_add_mcu", p, _ivec(controls), _ivec(levels), len(controls), int(target), _dptr(m))
 
 
 def qf_program_set_tiling(p: int, tile_qudits: int = 0, min_run_qudits: int = 0, max_ops: int = 0) -> None:
@@ -596,6 +635,10 @@ def apply_ops(s: int, ops: Iterable, params=None) -> None:
             qf_apply_swap(s, op.qudits[0], op.qudits[1])
         elif k == "u":
             qf_apply_gate(s, op.qudits, op.matrix)
+        elif k == "mcx":
+            qf_apply_mcx(s, op.qudits[:-1], op.qudits[-1], op.power)
+        elif k == "mcu":
+            qf_apply_mcu(s, op.qudits[:-1], op.levels, op.qudits[-1], op.matrix)
         else:
             raise ValueError(k)
 
@@ -623,6 +666,10 @@ def program_from_ops(d, n: int, ops: Iterable, fuse: bool = True) -> int:
             qf_program_add_swap(p, op.qudits[0], op.qudits[1])
         elif k == "u":
             qf_program_add_gate(p, op.qudits, op.matrix, dims)
+        elif k == "mcx":
+            qf_program_add_mcx(p, op.qudits[:-1], op.qudits[-1], op.power)
+        elif k == "mcu":
+            qf_program_add_mcu(p, op.qudits[:-1], op.levels, op.qudits[-1], op.matrix, dims)
         else:
             raise ValueError(k)
     qf_program_set_fusion(p, fuse)
