@@ -267,6 +267,23 @@ qf_status qf_program_add_mcu(qf_program *p, const int *controls, const int *leve
 /* Fusion control: enable != 0 (the default) plans fused passes; enable = 0
  * gives one pass per gate, in recorded order (the per-gate kernels).  Takes
  * effect at the next run. */
+/* Tile passes of a program are compiled for the current GPU when the program
+ * is first run after planning (NVRTC, about a second per program; compiled
+ * passes are shared by identical programs in the process): gate structure,
+ * register slots and offsets become literals and only the gate entries are
+ * passed per run.  enable = 0 runs the same passes through the library's
+ * generic tile kernel instead (no compilation).  Default 1.  Errors at run
+ * time: QF_ERR_UNSUPPORTED if NVRTC cannot be loaded, QF_ERR_CUDA (with the
+ * compiler log) if a pass fails to compile. */
+qf_status qf_program_set_jit(qf_program *p, int enable);
+/* Qudits held in registers per stage of a compiled tile pass (1..6; 0 = the
+ * default for d, 4 for d = 2 and 2 for d = 3..5 in complex64): more slots
+ * mean fewer shared-memory round trips and more registers per thread. */
+qf_status qf_program_set_stage_slots(qf_program *p, int slots);
+/* The CUDA source the program's tile passes compile from (for dtype dt), as
+ * a NUL-terminated string of *len bytes; buf (capacity cap) may be NULL to
+ * query the length.  Host only; nothing is compiled or launched. */
+qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, char *buf, size_t cap, size_t *len);
 qf_status qf_program_set_fusion(qf_program *p, int enable);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
@@ -329,6 +346,12 @@ qf_status qf_program_pass_times(qf_program *p, int max, float *ms, int *kind, do
  * number of passes, how many of them are single gates on the strided kernel,
  * and the largest number of ops in one pass.  Output pointers may be NULL. */
 qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_strided, int *max_ops);
+
+/* Register-stage statistics of the plan for dtype dt: tile passes, register
+ * stages over all tile passes (one shared-memory round trip and one barrier
+ * each) and ops (single-qudit runs already multiplied together).  Host-only
+ * planning; nothing is launched. */
+qf_status qf_program_stages(qf_program *p, qf_dtype dt, int *num_tile_passes, int *num_stages, int *num_ops);
 
 /* ---------------------------------------------------------------- batches
  * Many independent circuits of uneven qudit dimension and size (the

@@ -151,7 +151,7 @@ static cudaError_t launch_tile_d(const Launch &L, const TileArgs<R> &A, int d, s
     if (A.nstages > 0 && K > 0) {
         int dk = 1;
         for (int i = 0; i < K; ++i) dk *= d;
-        if (A.g.T / dk < kTileBlock) threads = kTileBlock / 2;
+        if (A.g.T / dk <= kTileBlock / 2) threads = kTileBlock / 2;
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, D>, threads, smem);

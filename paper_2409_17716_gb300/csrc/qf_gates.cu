@@ -603,7 +603,7 @@ std::vector<TStage> build_stages(std::vector<TOp> &ops, const TileGeom &g, int d
     const int nt = g.nt;
     // a tile narrower than K runs every op through shared memory (the kernels
     // treat an empty stage list that way, gradients included)
-    if (K == 0 || nt < K) return st;
+    if (K == 0 || nt < K || K > kMaxStageK) return st;
     auto legacy_kind = [](const TOp &o) { return o.kind == OP_SWAP || o.kind == OP_DENSEK; };
     auto has = [](const std::vector<int> &v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
     size_t i = 0;

@@ -198,6 +198,18 @@ TOp localize(const TOp &op, const TileGeom &g, const std::vector<int> &active, i
 qf_status program_shape(const qf_program *p, int *d, int *n);
 qf_status program_gates(const qf_program *p, std::vector<HGate> *out);
 
+// Tile passes of a program compiled at plan time (qf_jit.cu).
+struct JitProgram;
+qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
+                    int k_override, int num_sms, JitProgram **out);
+void jit_free(JitProgram *jp);
+qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
+                     int k_override, std::string *out);
+bool jit_pass_ready(const JitProgram *jp, size_t pi);
+bool jit_pass_global_pool(const JitProgram *jp, size_t pi);
+qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,
+                     const void *prepared, int npool, const void *gpool);
+
 // Immediate application of one resolved op on a mixed-dimension state.
 qf_status run_op_mixed(qf_state *s, const ROp &r);
 // Mixed-dimension programs: gate by gate forward, and the per-gate adjoint

@@ -130,7 +130,7 @@ static_assert(alignof(TOp) == 4, "TOp packs into shared memory after the matrix 
 // ops[first] is applied through shared memory instead.  The slot of an op's
 // target and control within the stage are stored in TOp::q[4] and q[5]
 // (-1: not a slot).
-constexpr int kMaxStageK = 4;
+constexpr int kMaxStageK = 6;   // compiled passes; the generic kernels use at most 4
 constexpr int kMaxGrad = 16;   // parametrised ops per adjoint pass (register accumulators)
 
 struct TStage {
@@ -145,7 +145,7 @@ struct TStage {
 // register blocks (psi, and lambda for the adjoint) fit without spilling.
 __host__ __device__ constexpr int stage_k(int d, bool adj, bool c128) {
     return d == 2   ? (adj ? (c128 ? 2 : 3) : (c128 ? 3 : 4))
-           : d == 3 ? ((adj && c128) ? 1 : 2)
+           : d == 3 ? ((adj && c128) ? 1 : (adj || c128) ? 2 : 3)
            : (d == 4 || d == 5) ? ((adj || c128) ? 1 : 2)
                                 : 0;
 }

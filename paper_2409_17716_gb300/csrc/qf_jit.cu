@@ -1,0 +1,720 @@
+// qf_jit.cu -- tile passes of recorded programs specialised at plan time.
+//
+// The generic tile kernel (k_tile.cu) interprets a pass: for every register
+// block of every tile it reads each op's kind, slots, levels and matrix
+// entries from shared memory and branches on them.  A program's passes are
+// fixed once it is planned, so each tile pass is instead emitted as CUDA C++
+// with everything structural written as literals -- the register slots and
+// element offsets of every stage, the level pairs, control slots, diagonal
+// masks, shift amounts and the tile geometry -- and compiled at run time with
+// NVRTC for the current GPU.  Only the numbers that change between runs (the
+// gate entries, which depend on the rotation angles) are passed, as kernel
+// parameters indexed by literals, so they reach the FMAs straight from the
+// constant bank.  Per amplitude a pass then costs its loads and stores, one
+// shared-memory round trip per register stage and the gates' own arithmetic.
+//
+// The arithmetic is that of the generic kernel (stage_device.cuh): complex64
+// entries prepared as (re, re, -im, im) for paired FP32 FMAs, complex128 in
+// FP64 FMAs.  NVRTC is loaded with dlopen and the driver entry points through
+// the runtime, so the library itself links against neither.
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <thread>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "qf_host.h"
+
+namespace qf {
+
+// ------------------------------------------------------------------ NVRTC and driver entry points
+namespace {
+
+struct Nvrtc {
+    nvrtcResult (*create)(nvrtcProgram *, const char *, const char *, int, const char *const *, const char *const *);
+    nvrtcResult (*compile)(nvrtcProgram, int, const char *const *);
+    nvrtcResult (*log_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*log)(nvrtcProgram, char *);
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
+    nvrtcResult (*cubin)(nvrtcProgram, char *);
+    nvrtcResult (*destroy)(nvrtcProgram *);
+};
+
+struct Driver {
+    CUresult (*module_load)(CUmodule *, const void *);
+    CUresult (*get_function)(CUfunction *, CUmodule, const char *);
+    CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                       void **, void **);
+    CUresult (*set_attribute)(CUfunction, CUfunction_attribute, int);
+    CUresult (*occupancy)(int *, CUfunction, int, size_t);
+};
+
+std::mutex g_mu;
+bool g_loaded = false;
+std::string g_load_err;
+Nvrtc g_nv;
+Driver g_drv;
+std::map<std::string, CUmodule> g_modules;   // generated source -> loaded module
+
+bool load_apis() {
+    if (g_loaded) return true;
+    if (!g_load_err.empty()) return false;
+    void *h = nullptr;
+    for (const char *name : {"libnvrtc.so.13", "libnvrtc.so", "libnvrtc.so.12"}) {
+        h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+        if (h) break;
+    }
+    if (!h) {
+        g_load_err = "NVRTC (libnvrtc.so) not found; it compiles the program's tile passes";
+        return false;
+    }
+    auto sym = [&](const char *s) { return dlsym(h, s); };
+    g_nv.create = (decltype(g_nv.create))sym("nvrtcCreateProgram");
+    g_nv.compile = (decltype(g_nv.compile))sym("nvrtcCompileProgram");
+    g_nv.log_size = (decltype(g_nv.log_size))sym("nvrtcGetProgramLogSize");
+    g_nv.log = (decltype(g_nv.log))sym("nvrtcGetProgramLog");
+    g_nv.cubin_size = (decltype(g_nv.cubin_size))sym("nvrtcGetCUBINSize");
+    g_nv.cubin = (decltype(g_nv.cubin))sym("nvrtcGetCUBIN");
+    g_nv.destroy = (decltype(g_nv.destroy))sym("nvrtcDestroyProgram");
+    if (!g_nv.create || !g_nv.compile || !g_nv.log_size || !g_nv.log || !g_nv.cubin_size || !g_nv.cubin ||
+        !g_nv.destroy) {
+        g_load_err = "NVRTC symbols missing";
+        return false;
+    }
+    auto drv = [&](const char *s, void **fp) {
+        cudaDriverEntryPointQueryResult q;
+        return cudaGetDriverEntryPointByVersion(s, fp, 13000, cudaEnableDefault, &q) == cudaSuccess &&
+               q == cudaDriverEntryPointSuccess && *fp;
+    };
+    if (!drv("cuModuleLoadData", (void **)&g_drv.module_load) ||
+        !drv("cuModuleGetFunction", (void **)&g_drv.get_function) || !drv("cuLaunchKernel", (void **)&g_drv.launch) ||
+        !drv("cuFuncSetAttribute", (void **)&g_drv.set_attribute) ||
+        !drv("cuOccupancyMaxActiveBlocksPerMultiprocessor", (void **)&g_drv.occupancy)) {
+        cudaGetLastError();
+        g_load_err = "CUDA driver entry points for module loading are unavailable";
+        return false;
+    }
+    g_loaded = true;
+    return true;
+}
+
+// Device helpers every generated kernel starts with.
+const char *kPrelude = R"(
+#if QJ_C64
+typedef float2 C;
+typedef float4 P;
+__device__ __forceinline__ C jm(const P p, C a) {
+    const C r = __fmul2_rn(make_float2(p.x, p.y), a);
+    return __ffma2_rn(make_float2(p.z, p.w), make_float2(a.y, a.x), r);
+}
+__device__ __forceinline__ C jma(const P p, C a, C acc) {
+    acc = __ffma2_rn(make_float2(p.x, p.y), a, acc);
+    return __ffma2_rn(make_float2(p.z, p.w), make_float2(a.y, a.x), acc);
+}
+__device__ __forceinline__ C jrm(float m, C a) { return __fmul2_rn(make_float2(m, m), a); }
+__device__ __forceinline__ C jrma(float m, C a, C acc) { return __ffma2_rn(make_float2(m, m), a, acc); }
+#define QJ_CP_BYTES "8"
+#define QJ_CP_KIND "ca"
+#else
+typedef double2 C;
+typedef double2 P;
+__device__ __forceinline__ C jm(const P p, C a) {
+    return make_double2(fma(p.x, a.x, -p.y * a.y), fma(p.x, a.y, p.y * a.x));
+}
+__device__ __forceinline__ C jma(const P p, C a, C acc) {
+    acc.x = fma(p.x, a.x, acc.x); acc.x = fma(-p.y, a.y, acc.x);
+    acc.y = fma(p.x, a.y, acc.y); acc.y = fma(p.y, a.x, acc.y);
+    return acc;
+}
+__device__ __forceinline__ C jrm(double m, C a) { return make_double2(m * a.x, m * a.y); }
+__device__ __forceinline__ C jrma(double m, C a, C acc) { return make_double2(fma(m, a.x, acc.x), fma(m, a.y, acc.y)); }
+#define QJ_CP_BYTES "16"
+#define QJ_CP_KIND "cg"
+#endif
+__device__ __forceinline__ unsigned qj_smem(const void *p) {
+    unsigned r;
+    asm("{ .reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t; }" : "=r"(r) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ void qj_cp(C *dst, const C *src) {
+    asm volatile("cp.async." QJ_CP_KIND ".shared.global [%0], [%1], " QJ_CP_BYTES ";\n" ::"r"(qj_smem(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void qj_wait() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory"); }
+)";
+
+constexpr int kParamPoolMax = 1800;   // pool entries passed as kernel parameters (16 bytes each)
+
+int ipow_i(int d, int e) {
+    int r = 1;
+    for (int i = 0; i < e; ++i) r *= d;
+    return r;
+}
+
+// Source of one tile pass.  `ops` are tile-local with their stage slots; the
+// pool offsets op.mat index the pass's prepared entries.
+struct PassSrc {
+    int d, T, SEG, nt, kA, nruns, K, threads;
+    bool c128, params;   // params: entries in the kernel parameters, else global
+    int npool;
+    std::vector<TOp> ops;
+    std::vector<TStage> stages;
+};
+
+class Gen {
+  public:
+    Gen(const PassSrc &p, std::ostringstream &o) : p_(p), o_(o), D_(p.d) {}
+
+    void kernel(const std::string &name) {
+        const int NG = std::max(1, 2 * p_.nruns + p_.kA);
+        const int NP = std::max(1, p_.params ? p_.npool : 1);
+        const int NA = p_.T / p_.SEG;
+        o_ << "struct __align__(16) A_" << name << " { C *psi; const P *gp; long long ntiles; long long geo[" << NG
+           << "]; P pool[" << NP << "]; };\n";
+        o_ << "extern \"C\" __global__ void __launch_bounds__(" << p_.threads << ") " << name
+           << "(const __grid_constant__ A_" << name << " A) {\n";
+        o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
+        o_ << "  __shared__ long long qj_base;\n";
+        o_ << "  C *tile = reinterpret_cast<C *>(qj_sm);\n";
+        o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm + " << (size_t)p_.T * elt() << ");\n";
+        o_ << "  const int tid = threadIdx.x;\n";
+        // run offsets of the active qudits
+        o_ << "  for (int a = tid; a < " << NA << "; a += " << p_.threads << ") {\n    long long o = 0; int rem = a;\n";
+        for (int i = p_.kA - 1; i >= 0; --i)
+            o_ << "    o += (long long)(rem % " << D_ << ") * A.geo[" << 2 * p_.nruns + i << "]; rem /= " << D_ << ";\n";
+        o_ << "    offA[a] = o;\n  }\n";
+        o_ << "  if (tid == 0) qj_base = qj_tile_base_" << name << "(A, blockIdx.x);\n";
+        o_ << "  __syncthreads();\n";
+        o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
+        o_ << "    const long long base = qj_base;\n";
+        o_ << "    const C *src = A.psi + base;\n";
+        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
+           << "; qj_cp(tile + e, src + offA[a] + (e - a * " << p_.SEG << ")); }\n";
+        o_ << "    qj_wait();\n    __syncthreads();\n";
+        for (const TStage &st : p_.stages) {
+            if (st.legacy) legacy(p_.ops[st.first]);
+            else stage(st);
+            o_ << "    __syncthreads();\n";
+        }
+        o_ << "    C *dst = A.psi + base;\n";
+        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
+           << "; dst[offA[a] + (e - a * " << p_.SEG << ")] = tile[e]; }\n";
+        o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
+           << "(A, t + gridDim.x);\n";
+        o_ << "    __syncthreads();\n  }\n}\n";
+    }
+
+    void tile_base_fn(const std::string &name) {
+        o_ << "struct A_" << name << ";\n";
+        o_ << "template <typename AT> __device__ __forceinline__ long long qj_tile_base_" << name
+           << "(const AT &A, long long t) {\n  long long base = 0;\n";
+        for (int r = 0; r < p_.nruns; ++r)
+            o_ << "  { const long long q = t / A.geo[" << r << "]; base += (t - q * A.geo[" << r << "]) * A.geo["
+               << p_.nruns + r << "]; t = q; }\n";
+        o_ << "  return base;\n}\n";
+    }
+
+    size_t elt() const { return p_.c128 ? 16 : 8; }
+
+  private:
+    const PassSrc &p_;
+    std::ostringstream &o_;
+    int D_;
+
+    std::string E(int k) const { return (p_.params ? "A.pool[" : "A.gp[") + std::to_string(k) + "]"; }
+    std::string Edyn(const std::string &expr) const { return (p_.params ? "A.pool[" : "A.gp[") + expr + "]"; }
+    static std::string V(int r) { return "v" + std::to_string(r); }
+
+    // ---------------------------------------------------------------- register stage
+    void stage(const TStage &st) {
+        const int K = p_.K, DK = ipow_i(D_, K), NBLK = p_.T / DK;
+        o_ << "    for (int blk = tid; blk < " << NBLK << "; blk += " << p_.threads << ") {\n      int b = blk;\n";
+        for (int i = 0; i < K; ++i)
+            o_ << "      { const int q = b / " << st.lsa[i] << "; b = q * " << st.lsa[i] * D_ << " + (b - q * "
+               << st.lsa[i] << "); }\n";
+        std::vector<int> off(DK);
+        for (int r = 0; r < DK; ++r) {
+            int o = 0;
+            for (int i = 0; i < K; ++i) o += ((r / ipow_i(D_, K - 1 - i)) % D_) * st.ls[i];
+            off[r] = o;
+        }
+        for (int r = 0; r < DK; ++r) o_ << "      C " << V(r) << " = tile[b + " << off[r] << "];\n";
+        for (int i = 0; i < st.nops; ++i) op(p_.ops[st.first + i]);
+        for (int r = 0; r < DK; ++r) o_ << "      tile[b + " << off[r] << "] = " << V(r) << ";\n";
+        o_ << "    }\n";
+    }
+
+    int rs(int S) const { return ipow_i(D_, p_.K - 1 - S); }
+    std::vector<int> fibres(int S) const {
+        const int RS = rs(S), DK = ipow_i(D_, p_.K);
+        std::vector<int> b;
+        for (int f = 0; f < DK / D_; ++f) b.push_back((f / RS) * RS * D_ + f % RS);
+        return b;
+    }
+    int slot_digit(int r, int slot) const { return (r / ipow_i(D_, p_.K - 1 - slot)) % D_; }
+
+    void pair_fibre(int b0, int RS, int J, int L, const std::string &e0, const std::string &e1, const std::string &e2,
+                    const std::string &e3, bool real) {
+        const std::string a = V(b0 + J * RS), c = V(b0 + L * RS);
+        o_ << "      { const C qa = " << a << ", qc = " << c << ";\n";
+        if (real) {
+            o_ << "        " << a << " = jrma(" << e1 << ".x, qc, jrm(" << e0 << ".x, qa));\n";
+            o_ << "        " << c << " = jrma(" << e3 << ".x, qc, jrm(" << e2 << ".x, qa)); }\n";
+        } else {
+            o_ << "        " << a << " = jma(" << e1 << ", qc, jm(" << e0 << ", qa));\n";
+            o_ << "        " << c << " = jma(" << e3 << ", qc, jm(" << e2 << ", qa)); }\n";
+        }
+    }
+
+    void shift_fibre(int b0, int RS, int sh) {
+        if (sh == 0) return;
+        o_ << "      {";
+        for (int m = 0; m < D_; ++m) o_ << " const C t" << m << " = " << V(b0 + m * RS) << ";";
+        for (int m = 0; m < D_; ++m) o_ << " " << V(b0 + ((m + sh) % D_) * RS) << " = t" << m << ";";
+        o_ << " }\n";
+    }
+
+    std::string outside_digit(int ls) const {
+        return "((b / " + std::to_string(ls) + ") % " + std::to_string(D_) + ")";
+    }
+
+    void op(const TOp &o) {
+        const int sa = o.q[4], sc = o.q[5];
+        const int m = o.mat;
+        const bool ctrl = is_controlled(o);
+        switch (o.kind) {
+        case OP_DENSE: {
+            const int RS = rs(sa);
+            for (int b0 : fibres(sa)) {
+                o_ << "      {";
+                for (int x = 0; x < D_; ++x) o_ << " const C x" << x << " = " << V(b0 + x * RS) << ";";
+                o_ << "\n";
+                for (int l = 0; l < D_; ++l) {
+                    std::string acc = "jm(" + E(m + l * D_) + ", x0)";
+                    for (int x = 1; x < D_; ++x) acc = "jma(" + E(m + l * D_ + x) + ", x" + std::to_string(x) + ", " + acc + ")";
+                    o_ << "        " << V(b0 + l * RS) << " = " << acc << ";\n";
+                }
+                o_ << "      }\n";
+            }
+            break;
+        }
+        case OP_PAIR:
+        case OP_CPAIR: {
+            const int RS = rs(sa);
+            const bool real = o.s == 1;
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { const int mb = " << m
+                   << " + 4 * cl;\n";
+                for (int b0 : fibres(sa))
+                    pair_fibre(b0, RS, o.j, o.k, Edyn("mb"), Edyn("mb + 1"), Edyn("mb + 2"), Edyn("mb + 3"), real);
+                o_ << "      } }\n";
+                break;
+            }
+            for (int b0 : fibres(sa)) {
+                int mb = m;
+                if (ctrl) {
+                    const int cl = slot_digit(b0, sc);
+                    if (cl == 0) continue;
+                    mb = m + 4 * cl;
+                }
+                pair_fibre(b0, RS, o.j, o.k, E(mb), E(mb + 1), E(mb + 2), E(mb + 3), real);
+            }
+            break;
+        }
+        case OP_DIAG:
+        case OP_CDIAG: {
+            if (sa < 0) {   // target outside the stage: one phase for the block
+                o_ << "      { const int dg = " << outside_digit(o.lsa) << "; if ((" << o.mask
+                   << " >> dg) & 1) { const P ph = " << Edyn(std::to_string(m) + " + dg") << ";";
+                const int DK = ipow_i(D_, p_.K);
+                for (int r = 0; r < DK; ++r) o_ << " " << V(r) << " = jm(ph, " << V(r) << ");";
+                o_ << " } }\n";
+                break;
+            }
+            const int RS = rs(sa);
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { const int mb = " << m << " + "
+                   << D_ << " * cl;";
+                for (int b0 : fibres(sa))
+                    for (int l = 0; l < D_; ++l)
+                        if ((o.mask >> l) & 1)
+                            o_ << " " << V(b0 + l * RS) << " = jm(" << Edyn("mb + " + std::to_string(l)) << ", "
+                               << V(b0 + l * RS) << ");";
+                o_ << " } }\n";
+                break;
+            }
+            for (int b0 : fibres(sa)) {
+                int mb = m;
+                if (ctrl) {
+                    const int cl = slot_digit(b0, sc);
+                    if (cl == 0) continue;
+                    mb = m + D_ * cl;
+                }
+                o_ << "     ";
+                for (int l = 0; l < D_; ++l)
+                    if ((o.mask >> l) & 1) o_ << " " << V(b0 + l * RS) << " = jm(" << E(mb + l) << ", " << V(b0 + l * RS) << ");";
+                o_ << "\n";
+            }
+            break;
+        }
+        case OP_SHIFT:
+        case OP_CSHIFT: {
+            const int RS = rs(sa);
+            if (ctrl && sc < 0) {
+                o_ << "      { const int sh = (" << o.s << " * " << outside_digit(o.lsc) << ") % " << D_ << ";\n";
+                for (int sh = 1; sh < D_; ++sh) {
+                    o_ << "      if (sh == " << sh << ") {\n";
+                    for (int b0 : fibres(sa)) shift_fibre(b0, RS, sh);
+                    o_ << "      }\n";
+                }
+                o_ << "      }\n";
+                break;
+            }
+            for (int b0 : fibres(sa)) {
+                const int sh = ctrl ? (o.s * slot_digit(b0, sc)) % D_ : o.s % D_;
+                shift_fibre(b0, RS, sh);
+            }
+            break;
+        }
+        default:
+            break;
+        }
+    }
+
+    // ---------------------------------------------------------------- shared-memory ops
+    void legacy(const TOp &o) {
+        if (o.kind == OP_SWAP) {
+            const int la = o.lsa, lc = o.lsc;
+            o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") {\n";
+            o_ << "      const int x = (e / " << la << ") % " << D_ << ", y = (e / " << lc << ") % " << D_ << ";\n";
+            o_ << "      if (x < y) { const int e2 = e + (y - x) * " << (la - lc)
+               << "; const C t0 = tile[e]; tile[e] = tile[e2]; tile[e2] = t0; }\n    }\n";
+            return;
+        }
+        // OP_DENSEK: entries always in global memory (up to 64 x 64)
+        const int K = o.nq;
+        std::vector<int> ls(K);
+        int DK = 1;
+        for (int i = 0; i < K; ++i) {
+            ls[i] = ipow_i(D_, p_.nt - 1 - o.q[i]);
+            DK *= D_;
+        }
+        std::vector<int> asc = ls;
+        std::sort(asc.begin(), asc.end());
+        o_ << "    for (int g = tid; g < " << p_.T / DK << "; g += " << p_.threads << ") {\n      int b = g;\n";
+        for (int s : asc) o_ << "      { const int q = b / " << s << "; b = q * " << s * D_ << " + (b - q * " << s << "); }\n";
+        o_ << "      const int offs[" << DK << "] = {";
+        for (int r = 0; r < DK; ++r) {
+            int off = 0, rr = r;
+            for (int i = K - 1; i >= 0; --i) { off += (rr % D_) * ls[i]; rr /= D_; }
+            o_ << (r ? ", " : "") << off;
+        }
+        o_ << "};\n      C xs[" << DK << "];\n";
+        o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = tile[b + offs[r]];\n";
+        o_ << "      for (int r = 0; r < " << DK << "; ++r) { C acc = jm(A.gp[" << o.mat << " + r * " << DK
+           << "], xs[0]); for (int x = 1; x < " << DK << "; ++x) acc = jma(A.gp[" << o.mat << " + r * " << DK
+           << " + x], xs[x], acc); tile[b + offs[r]] = acc; }\n    }\n";
+    }
+};
+
+std::string cuda_err(CUresult r) { return "CUresult " + std::to_string((int)r); }
+
+}  // namespace
+
+// Register slots of a generated register stage.
+int jit_stage_k(int d, bool c128) {
+    if (c128) return d == 2 ? 3 : (d == 3 || d == 4) ? 2 : 1;
+    return d == 2 ? 4 : d <= 5 ? 2 : 1;
+}
+
+struct JitPassInfo {
+    CUfunction fn = nullptr;
+    int threads = 256;
+    size_t smem = 0;
+    int grid = 1;
+    bool params = true;     // pool in the kernel parameters
+    int npool = 0;
+    size_t arg_bytes = 0, pool_off = 0;
+    int NG = 1;
+};
+
+struct JitProgram {
+    std::vector<JitPassInfo> passes;   // per plan pass (fn == nullptr for strided / mc passes)
+};
+
+// CUDA source of every tile pass of a plan (one translation unit per pass,
+// empty for strided / multi-controlled passes), and the launch shape of each.
+// `ops` are the passes' localized ops in pool order (op.mat already set), one
+// vector per pass; k_override > 0 sets the register slots per stage.
+static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops,
+                                            int d, bool c128, int k_override, JitProgram *jp,
+                                            std::vector<std::string> &names) {
+    jp->passes.resize(plan.size());
+    names.assign(plan.size(), std::string());
+    std::vector<std::string> out(plan.size());
+    std::vector<PassSrc> specs(plan.size());
+    for (size_t pi = 0; pi < plan.size(); ++pi) {
+        const PassPlan &pp = plan[pi];
+        if (pp.strided || pp.mc) continue;
+        PassSrc &ps = specs[pi];
+        ps.d = d;
+        ps.c128 = c128;
+        ps.T = pp.geom.T;
+        ps.SEG = pp.geom.SEG;
+        ps.nt = pp.geom.nt;
+        ps.kA = pp.geom.kA;
+        ps.nruns = pp.geom.nruns;
+        ps.K = std::min(k_override > 0 ? k_override : jit_stage_k(d, c128), pp.geom.nt);
+        ps.ops = ops[pi];
+        ps.stages = build_stages(ps.ops, pp.geom, d, ps.K);
+        ops[pi] = ps.ops;   // the stage slots written by build_stages
+        int npool = 0;
+        bool dense_k = false;
+        for (const TOp &o : ps.ops) dense_k |= o.kind == OP_DENSEK;
+        // pool size: one past the largest entry any op uses
+        for (const TOp &o : ps.ops) {
+            int cnt = 0;
+            switch (o.kind) {
+            case OP_DENSE: cnt = d * d; break;
+            case OP_PAIR: cnt = 4; break;
+            case OP_DIAG: cnt = d; break;
+            case OP_CPAIR: cnt = 4 * d; break;
+            case OP_CDIAG: cnt = d * d; break;
+            case OP_DENSEK: { int K = 1; for (int i = 0; i < o.nq; ++i) K *= d; cnt = K * K; break; }
+            default: cnt = 0;
+            }
+            npool = std::max(npool, o.mat + cnt);
+        }
+        ps.npool = npool;
+        ps.params = npool <= kParamPoolMax && !dense_k;
+        const int DK = ipow_i(d, ps.K);
+        ps.threads = (ps.T / DK <= 128) ? 128 : 256;
+        std::ostringstream nm;
+        nm << "k_tile_jit_d" << d << (c128 ? "_c128_" : "_c64_") << pi;
+        names[pi] = nm.str();
+        std::ostringstream src;
+        src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n" << kPrelude;
+        Gen g(ps, src);
+        g.tile_base_fn(names[pi]);
+        g.kernel(names[pi]);
+        out[pi] = src.str();
+        JitPassInfo &ji = jp->passes[pi];
+        ji.threads = ps.threads;
+        ji.smem = (size_t)ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;
+        ji.params = ps.params;
+        ji.npool = npool;
+        ji.NG = std::max(1, 2 * ps.nruns + ps.kA);
+        ji.pool_off = (24 + 8 * (size_t)ji.NG + 15) & ~(size_t)15;
+        ji.arg_bytes = ji.pool_off + 16 * (size_t)std::max(1, ps.params ? npool : 1);
+    }
+    return out;
+}
+
+qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
+                     int k_override, std::string *out) {
+    JitProgram jp;
+    std::vector<std::string> names;
+    std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, &jp, names);
+    out->clear();
+    for (const std::string &x : srcs)
+        if (!x.empty()) *out += "// ---- translation unit\n" + x;
+    return QF_OK;
+}
+
+namespace {
+
+// FNV-1a over the source and the target: the name of a cached cubin.
+std::string source_key(const std::string &src, const std::string &arch) {
+    uint64_t h = 1469598103934665603ull;
+    for (unsigned char c : src + "|" + arch) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    char buf[32];
+    snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)h);
+    return std::string(buf) + "_" + std::to_string(src.size());
+}
+
+// Cubin cache directory next to the library (created on first use).
+std::string cache_dir() {
+    Dl_info info;
+    std::string dir;
+    if (dladdr((void *)&cache_dir, &info) && info.dli_fname) {
+        dir = info.dli_fname;
+        const size_t k = dir.rfind('/');
+        dir = (k == std::string::npos ? std::string(".") : dir.substr(0, k)) + "/jit_cache";
+    }
+    return dir;
+}
+
+bool read_file(const std::string &path, std::vector<char> &out) {
+    FILE *f = fopen(path.c_str(), "rb");
+    if (!f) return false;
+    fseek(f, 0, SEEK_END);
+    const long n = ftell(f);
+    fseek(f, 0, SEEK_SET);
+    out.resize(n > 0 ? (size_t)n : 0);
+    const bool ok = n > 0 && fread(out.data(), 1, (size_t)n, f) == (size_t)n;
+    fclose(f);
+    return ok;
+}
+
+void write_file(const std::string &path, const std::vector<char> &data) {
+    const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    const bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+    fclose(f);
+    if (ok) rename(tmp.c_str(), path.c_str());
+    else remove(tmp.c_str());
+}
+
+// Compiles one translation unit; returns false with the log on failure.
+bool nvrtc_compile(const std::string &code, const std::string &arch, std::vector<char> &cubin, std::string &log) {
+    nvrtcProgram prog;
+    if (g_nv.create(&prog, code.c_str(), "qf_tile_pass.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        log = "program creation failed";
+        return false;
+    }
+    const char *opts[] = {arch.c_str(), "-std=c++17", "-default-device"};
+    const nvrtcResult cr = g_nv.compile(prog, 3, opts);
+    if (cr != NVRTC_SUCCESS) {
+        size_t ls = 0;
+        g_nv.log_size(prog, &ls);
+        log.assign(ls, '\0');
+        if (ls) g_nv.log(prog, &log[0]);
+        g_nv.destroy(&prog);
+        return false;
+    }
+    size_t cs = 0;
+    g_nv.cubin_size(prog, &cs);
+    cubin.resize(cs);
+    g_nv.cubin(prog, cubin.data());
+    g_nv.destroy(&prog);
+    return true;
+}
+
+}  // namespace
+
+// Builds (or reuses) the kernels of every tile pass of a plan: cached modules
+// of this process first, then cubins cached on disk, then NVRTC (passes
+// compiled in parallel threads).
+qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
+                    int k_override, int num_sms, JitProgram **out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!load_apis()) return set_error(QF_ERR_UNSUPPORTED, g_load_err);
+    JitProgram *jp = new JitProgram();
+    std::vector<std::string> names;
+    const std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, jp, names);
+    int major = 10, minor = 3, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    const std::string arch = "--gpu-architecture=sm_" + std::to_string(major) + std::to_string(minor) + "a";
+    const std::string dir = cache_dir();
+    if (!dir.empty()) mkdir(dir.c_str(), 0755);
+    const size_t np = plan.size();
+    std::vector<std::vector<char>> cubins(np);
+    std::vector<std::string> keys(np), logs(np);
+    std::vector<char> need(np, 0);
+    for (size_t pi = 0; pi < np; ++pi) {
+        if (srcs[pi].empty() || g_modules.count(srcs[pi])) continue;
+        keys[pi] = source_key(srcs[pi], arch);
+        if (!dir.empty() && read_file(dir + "/" + keys[pi] + ".cubin", cubins[pi])) continue;
+        need[pi] = 1;
+    }
+    std::vector<std::thread> pool;
+    std::vector<char> ok(np, 1);
+    std::atomic<size_t> next(0);
+    const unsigned nthreads = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    for (unsigned w = 0; w < nthreads; ++w)
+        pool.emplace_back([&]() {
+            for (size_t pi = next++; pi < np; pi = next++)
+                if (need[pi]) ok[pi] = nvrtc_compile(srcs[pi], arch, cubins[pi], logs[pi]) ? 1 : 0;
+        });
+    for (auto &t : pool) t.join();
+    cudaFree(0);   // the runtime's primary context is current
+    for (size_t pi = 0; pi < np; ++pi) {
+        if (srcs[pi].empty()) continue;
+        if (!ok[pi]) {
+            delete jp;
+            return set_error(QF_ERR_CUDA, "NVRTC compile of a tile pass failed: " + logs[pi].substr(0, 2000));
+        }
+        CUmodule mod = nullptr;
+        auto it = g_modules.find(srcs[pi]);
+        if (it != g_modules.end()) {
+            mod = it->second;
+        } else {
+            const CUresult lr = g_drv.module_load(&mod, cubins[pi].data());
+            if (lr != CUDA_SUCCESS) {
+                delete jp;
+                return set_error(QF_ERR_CUDA, "loading a compiled tile pass failed: " + cuda_err(lr));
+            }
+            g_modules[srcs[pi]] = mod;
+            if (need[pi] && !dir.empty()) write_file(dir + "/" + keys[pi] + ".cubin", cubins[pi]);
+        }
+        JitPassInfo &ji = jp->passes[pi];
+        CUresult r = g_drv.get_function(&ji.fn, mod, names[pi].c_str());
+        if (r == CUDA_SUCCESS && ji.smem > 48 * 1024)
+            r = g_drv.set_attribute(ji.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ji.smem);
+        int per_sm = 0;
+        if (r == CUDA_SUCCESS) r = g_drv.occupancy(&per_sm, ji.fn, ji.threads, ji.smem);
+        if (r != CUDA_SUCCESS || per_sm < 1) {
+            delete jp;
+            return set_error(QF_ERR_CUDA, "tile pass kernel setup failed: " + cuda_err(r));
+        }
+        long long grid = (long long)per_sm * num_sms;
+        if (grid > plan[pi].geom.ntiles) grid = plan[pi].geom.ntiles;
+        ji.grid = (int)grid;
+    }
+    *out = jp;
+    return QF_OK;
+}
+
+void jit_free(JitProgram *jp) { delete jp; }
+
+bool jit_pass_ready(const JitProgram *jp, size_t pi) { return jp && pi < jp->passes.size() && jp->passes[pi].fn; }
+
+// Whether pass pi takes its entries from a global pool (the caller uploads
+// the prepared entries and passes their device address).
+bool jit_pass_global_pool(const JitProgram *jp, size_t pi) { return !jp->passes[pi].params; }
+
+// Launches pass pi.  `prepared` holds the pass's entries in kernel form
+// (complex64: (re, re, -im, im) as float4; complex128: (re, im) as double2),
+// 16 bytes each; gpool is their device copy when the pass reads them globally.
+qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,
+                     const void *prepared, int npool, const void *gpool) {
+    const JitPassInfo &ji = jp->passes[pi];
+    std::vector<unsigned char> args(ji.arg_bytes, 0);
+    std::memcpy(args.data(), &psi, 8);
+    std::memcpy(args.data() + 8, &gpool, 8);
+    std::memcpy(args.data() + 16, &g.ntiles, 8);
+    long long geo[2 * (kMaxActive + 1) + kMaxActive] = {};
+    for (int r = 0; r < g.nruns; ++r) {
+        geo[r] = g.runM[r];
+        geo[g.nruns + r] = g.runS[r];
+    }
+    for (int i = 0; i < g.kA; ++i) geo[2 * g.nruns + i] = g.strideA[i];
+    std::memcpy(args.data() + 24, geo, 8 * (size_t)(2 * g.nruns + g.kA));
+    if (ji.params && npool > 0) std::memcpy(args.data() + ji.pool_off, prepared, 16 * (size_t)npool);
+    void *kp[] = {args.data()};
+    const CUresult r = g_drv.launch(ji.fn, (unsigned)ji.grid, 1, 1, (unsigned)ji.threads, 1, 1, (unsigned)ji.smem,
+                                    (CUstream)stream, kp, nullptr);
+    if (r != CUDA_SUCCESS) return set_error(QF_ERR_CUDA, "tile pass launch failed: " + cuda_err(r));
+    return QF_OK;
+}
+
+}  // namespace qf

@@ -22,6 +22,10 @@ struct qf_program {
     int num_params = 0;
     bool fuse = true;
     bool stages = true;                // register stages in tile passes
+    bool jit = true;                   // tile passes compiled at plan time (qf_jit.cu)
+    int jit_k = 0;                     // register slots per compiled stage (0: default per d)
+    JitProgram *jitp = nullptr;        // compiled passes of `plan` (nullptr: not built)
+    bool jit_c128 = false;
     int tile_qudits = 0, min_run_qudits = 0, max_ops = 0;   // planner overrides (0: default)
     bool plan_valid = false;
     bool plan_c128 = false;
@@ -159,6 +163,141 @@ static qf_status upload(qf_program *p, qf_state *s, const std::vector<unsigned c
     return QF_OK;
 }
 
+// Prepared entries of a resolved op for a compiled tile pass: complex64 as
+// (re, re, -im, im), complex128 as (re, im); 16 bytes each.
+template <typename R>
+static void append_prepared(const ROp &r, std::vector<unsigned char> &out) {
+    for (const cd &z : r.m) {
+        if (sizeof(R) == 4) {
+            const float v[4] = {(float)z.real(), (float)z.real(), -(float)z.imag(), (float)z.imag()};
+            out.insert(out.end(), (const unsigned char *)v, (const unsigned char *)v + 16);
+        } else {
+            const double v[2] = {z.real(), z.imag()};
+            out.insert(out.end(), (const unsigned char *)v, (const unsigned char *)v + 16);
+        }
+    }
+}
+
+static void drop_jit(qf_program *p) {
+    if (p->jitp) {
+        jit_free(p->jitp);
+        p->jitp = nullptr;
+    }
+}
+
+// Localized ops of every tile pass in pool order (entries at `params`).
+static std::vector<std::vector<TOp>> jit_ops(const qf_program *p, const double *params) {
+    std::vector<std::vector<TOp>> ops(p->plan.size());
+    for (size_t pi = 0; pi < p->plan.size(); ++pi) {
+        const PassPlan &pp = p->plan[pi];
+        if (pp.strided || pp.mc) continue;
+        int off = 0;
+        for (const auto &grp : pp.groups) {
+            ROp r = resolve_group(p->gates, grp, p->d, params);
+            TOp o = localize(r.op, pp.geom, pp.active, p->n, p->d);
+            o.mat = off;
+            off += (int)r.m.size();
+            ops[pi].push_back(o);
+        }
+    }
+    return ops;
+}
+
+// Forward run with the passes compiled for this plan.
+template <typename R>
+static qf_status run_program_jit(qf_program *p, qf_state *s, const double *params) {
+    using C = cplx<R>;
+    const int d = p->d, n = p->n;
+    const bool c128 = sizeof(R) == 8;
+    if (!p->jitp || p->jit_c128 != c128) {
+        drop_jit(p);
+        std::vector<std::vector<TOp>> ops = jit_ops(p, params);
+        qf_status st = jit_build(p->plan, ops, d, c128, p->jit_k, s->num_sms, &p->jitp);
+        if (st != QF_OK) return st;
+        p->jit_c128 = c128;
+    }
+    // entries of every pass at these parameters; passes reading them from
+    // global memory get a copy in the program's upload buffer
+    const size_t np = p->plan.size();
+    std::vector<std::vector<unsigned char>> prep(np);
+    std::vector<ROp> single(np);
+    std::vector<size_t> goff(np, 0);
+    std::vector<unsigned char> host;
+    for (size_t pi = 0; pi < np; ++pi) {
+        const PassPlan &pp = p->plan[pi];
+        if (pp.strided || pp.mc) {
+            single[pi] = resolve_group(p->gates, pp.groups[0], d, params);
+            continue;
+        }
+        for (const auto &grp : pp.groups) append_prepared<R>(resolve_group(p->gates, grp, d, params), prep[pi]);
+        if (jit_pass_global_pool(p->jitp, pi)) {
+            goff[pi] = align16(host.size());
+            host.resize(goff[pi] + prep[pi].size());
+            std::memcpy(host.data() + goff[pi], prep[pi].data(), prep[pi].size());
+        }
+    }
+    qf_status ust = upload(p, s, host);
+    if (ust != QF_OK) return ust;
+    Launch L;
+    L.stream = s->stream;
+    L.num_sms = s->num_sms;
+    C *psi = reinterpret_cast<C *>(s->data);
+    int launched = 0;
+    int prev_ev = -1;
+    if (p->timing) {
+        const size_t need = p->tused + np + 1;
+        while (p->tev.size() < need) {
+            cudaEvent_t ev;
+            QF_CUDA(cudaEventCreate(&ev));
+            p->tev.push_back(ev);
+        }
+        prev_ev = p->tused++;
+        QF_CUDA(cudaEventRecord(p->tev[prev_ev], s->stream));
+    }
+    const long long N = ipow_ll(d, n);
+    for (size_t pi = 0; pi < np; ++pi) {
+        const PassPlan &pp = p->plan[pi];
+        if (pp.strided || pp.mc) {
+            const TOp &o = single[pi].op;
+            if ((o.kind == OP_SHIFT && o.s == 0) || (o.kind == OP_DIAG && o.mask == 0) ||
+                (o.kind == OP_MCSHIFT && o.s == 0))
+                continue;
+            std::vector<C> m(single[pi].m.size());
+            for (size_t i = 0; i < m.size(); ++i) m[i] = mk<R>((R)single[pi].m[i].real(), (R)single[pi].m[i].imag());
+            if (p->timing) {
+                p->tkind.push_back(1);
+                p->tbytes.push_back(pp.mc ? 2.0 * sizeof(C) * (double)N : strided_bytes(o, d, N, (int)sizeof(C)));
+            }
+            cudaError_t e = pp.mc ? launch_mc<R>(L, psi, uniform_shape(d, n), o, m.data(), (int)m.size())
+                                  : launch_strided<R>(L, psi, d, n, o, m.data(), (int)m.size());
+            if (e != cudaSuccess) return cuda_error(e, "program pass");
+        } else {
+            if (p->timing) {
+                p->tkind.push_back(0);
+                p->tbytes.push_back(2.0 * sizeof(C) * (double)N);
+            }
+            const void *gp = jit_pass_global_pool(p->jitp, pi)
+                                 ? (const void *)(reinterpret_cast<const unsigned char *>(p->d_buf) + goff[pi])
+                                 : nullptr;
+            qf_status st = jit_launch(p->jitp, pi, s->stream, psi, pp.geom, prep[pi].data(),
+                                      (int)(prep[pi].size() / 16), gp);
+            if (st != QF_OK) return st;
+        }
+        ++launched;
+        if (p->timing) {
+            const int cur = p->tused++;
+            QF_CUDA(cudaEventRecord(p->tev[cur], s->stream));
+            p->tbefore.push_back(prev_ev);
+            p->tafter.push_back(cur);
+            prev_ev = cur;
+        }
+    }
+    QF_CUDA(cudaEventRecord(p->done_ev, s->stream));
+    p->ran = true;
+    p->last_passes = launched;
+    return QF_OK;
+}
+
 template <typename R>
 static qf_status run_program_t(qf_program *p, qf_state *s, const double *params) {
     using C = cplx<R>;
@@ -168,7 +307,9 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         p->plan = plan_passes(p->gates, d, n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->plan_valid = true;
         p->plan_c128 = c128;
+        drop_jit(p);
     }
+    if (p->jit) return run_program_jit<R>(p, s, params);
     // resolve every pass; tile passes get their op list + pool in one buffer
     struct Built {
         bool strided = false, mc = false;
@@ -653,6 +794,7 @@ qf_status qf_program_free(qf_program *p) {
     for (cudaEvent_t ev : p->tev) cudaEventDestroy(ev);
     if (p->d_rows) cudaFree(p->d_rows);
     if (p->d_res) cudaFree(p->d_res);
+    drop_jit(p);
     if (p->h_res) cudaFreeHost(p->h_res);
     if (p->up_ev) cudaEventDestroy(p->up_ev);
     if (p->done_ev) cudaEventDestroy(p->done_ev);
@@ -675,6 +817,7 @@ static qf_status add(qf_program *p, HGate g) {
     p->gates.push_back(std::move(g));
     p->plan_valid = false;
     p->adj_valid = false;
+    drop_jit(p);
     return QF_OK;
 }
 
@@ -778,6 +921,46 @@ qf_status qf_program_set_tiling(qf_program *p, int tile_qudits, int min_run_qudi
     p->max_ops = max_ops;
     p->plan_valid = false;
     p->adj_valid = false;
+    drop_jit(p);
+    return QF_OK;
+}
+
+qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, char *buf, size_t cap, size_t *len) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (p->mixed) return set_error(QF_ERR_UNSUPPORTED, "mixed-dimension programs run gate by gate");
+    const bool c128 = dt == QF_C128;
+    if (!p->plan_valid || p->plan_c128 != c128) {
+        p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
+        p->plan_valid = true;
+        p->plan_c128 = c128;
+        drop_jit(p);
+    }
+    std::vector<double> zeros((size_t)std::max(1, p->num_params), 0.0);
+    std::vector<std::vector<TOp>> ops = jit_ops(p, zeros.data());
+    std::string src;
+    qf_status st = jit_source(p->plan, ops, p->d, c128, p->jit_k, &src);
+    if (st != QF_OK) return st;
+    if (len) *len = src.size() + 1;
+    if (buf && cap > 0) {
+        const size_t nb = std::min(cap - 1, src.size());
+        std::memcpy(buf, src.data(), nb);
+        buf[nb] = 0;
+    }
+    return QF_OK;
+}
+
+qf_status qf_program_set_jit(qf_program *p, int enable) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    p->jit = enable != 0;
+    drop_jit(p);
+    return QF_OK;
+}
+
+qf_status qf_program_set_stage_slots(qf_program *p, int slots) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (slots < 0 || slots > kMaxStageK) return set_error(QF_ERR_ARG, "stage slots must be in [0, 6]");
+    p->jit_k = slots;
+    drop_jit(p);
     return QF_OK;
 }
 
@@ -786,6 +969,7 @@ qf_status qf_program_set_fusion(qf_program *p, int enable) {
     p->fuse = enable != 0;
     p->plan_valid = false;
     p->adj_valid = false;
+    drop_jit(p);
     return QF_OK;
 }
 
@@ -821,6 +1005,7 @@ qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_
         p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->plan_valid = true;
         p->plan_c128 = c128;
+        drop_jit(p);
     }
     int ns = 0, mo = 0;
     for (const PassPlan &pp : p->plan) {
@@ -830,6 +1015,40 @@ qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_
     if (num_passes) *num_passes = (int)p->plan.size();
     if (num_strided) *num_strided = ns;
     if (max_ops) *max_ops = mo;
+    return QF_OK;
+}
+
+qf_status qf_program_stages(qf_program *p, qf_dtype dt, int *num_tile_passes, int *num_stages, int *num_ops) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (p->mixed) {
+        if (num_tile_passes) *num_tile_passes = 0;
+        if (num_stages) *num_stages = 0;
+        if (num_ops) *num_ops = (int)p->gates.size();
+        return QF_OK;
+    }
+    const bool c128 = dt == QF_C128;
+    if (!p->plan_valid || p->plan_c128 != c128) {
+        p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
+        p->plan_valid = true;
+        p->plan_c128 = c128;
+        drop_jit(p);
+    }
+    int tp = 0, ns = 0, no = 0;
+    for (const PassPlan &pp : p->plan) {
+        if (pp.strided || pp.mc) continue;
+        std::vector<TOp> ops;
+        for (const auto &grp : pp.groups) {
+            ROp r = resolve_group(p->gates, grp, p->d, nullptr);
+            ops.push_back(localize(r.op, pp.geom, pp.active, p->n, p->d));
+        }
+        std::vector<TStage> stages = build_stages(ops, pp.geom, p->d, stage_k(p->d, false, c128));
+        ++tp;
+        ns += stages.empty() ? (int)ops.size() : (int)stages.size();
+        no += (int)ops.size();
+    }
+    if (num_tile_passes) *num_tile_passes = tp;
+    if (num_stages) *num_stages = ns;
+    if (num_ops) *num_ops = no;
     return QF_OK;
 }
 

@@ -83,10 +83,14 @@ _PROTOS = {
     "qf_program_add_mcx": (_int, [_vp, _c.POINTER(_int), _int, _int, _int]),
     "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
+    "qf_program_set_jit": (_int, [_vp, _int]),
+    "qf_program_set_stage_slots": (_int, [_vp, _int]),
+    "qf_program_jit_source": (_int, [_vp, _int, _c.c_char_p, _c.c_size_t, _c.POINTER(_c.c_size_t)]),
     "qf_program_set_tiling": (_int, [_vp, _int, _int, _int]),
     "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
     "qf_program_last_passes": (_int, [_vp]),
     "qf_program_plan": (_int, [_vp, _int, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
+    "qf_program_stages": (_int, [_vp, _int, _c.POINTER(_int), _c.POINTER(_int), _c.POINTER(_int)]),
     "qf_program_adjoint": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _vp, _vp]),
     "qf_program_gradient": (_int, [_vp, _vp, _vp, _c.POINTER(_dbl), _c.POINTER(_dbl), _c.POINTER(_dbl),
                                    _c.POINTER(_dbl)]),
@@ -436,6 +440,24 @@ def qf_program_set_tiling(p: int, tile_qudits: int = 0, min_run_qudits: int = 0,
     _call("qf_program_set_tiling", p, int(tile_qudits), int(min_run_qudits), int(max_ops))
 
 
+def qf_program_set_jit(p: int, enable: bool) -> None:
+    """Compiled (True, default) or generic (False) tile passes."""
+    _call("qf_program_set_jit", p, 1 if enable else 0)
+
+
+def qf_program_set_stage_slots(p: int, slots: int = 0) -> None:
+    _call("qf_program_set_stage_slots", p, int(slots))
+
+
+def qf_program_jit_source(p: int, dtype: int = QF_C64) -> str:
+    """CUDA source of the program's compiled tile passes."""
+    n = _c.c_size_t()
+    _call("qf_program_jit_source", p, dtype, None, 0, _c.byref(n))
+    buf = _c.create_string_buffer(n.value)
+    _call("qf_program_jit_source", p, dtype, buf, n.value, _c.byref(n))
+    return buf.value.decode()
+
+
 def qf_program_set_fusion(p: int, enable: bool) -> None:
     _call("qf_program_set_fusion", p, 1 if enable else 0)
 
@@ -561,6 +583,13 @@ def qf_program_plan(p: int, dtype: int = QF_C64):
     """(passes, strided passes, max ops per pass) of the program's plan."""
     a, b, c = _int(), _int(), _int()
     _call("qf_program_plan", p, dtype, _c.byref(a), _c.byref(b), _c.byref(c))
+    return a.value, b.value, c.value
+
+
+def qf_program_stages(p: int, dtype: int = QF_C64):
+    """(tile passes, register stages, ops) of the program's plan."""
+    a, b, c = _int(), _int(), _int()
+    _call("qf_program_stages", p, dtype, _c.byref(a), _c.byref(b), _c.byref(c))
     return a.value, b.value, c.value
 
 

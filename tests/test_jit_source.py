@@ -1,0 +1,81 @@
+"""The CUDA source a program's compiled tile passes are built from compiles
+with NVRTC for sm_103a (host only, no GPU): every gate kind, controls inside
+and outside a register stage, shared-memory SWAP and multi-qudit gates,
+complex64 and complex128, default and overridden stage slots."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_2409_17716_gb300 import qf, workloads as W
+
+
+def _nvrtc():
+    for name in ("libnvrtc.so.13", "libnvrtc.so", os.path.join("/usr/local/cuda/lib64", "libnvrtc.so")):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("NVRTC not available")
+
+
+def _compile(L, src):
+    prog = ctypes.c_void_p()
+    assert L.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"t.cu", 0, None, None) == 0
+    opts = [b"--gpu-architecture=sm_103a", b"-std=c++17", b"-default-device"]
+    rc = L.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    n = ctypes.c_size_t()
+    L.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(max(n.value, 1))
+    L.nvrtcGetProgramLog(prog, log)
+    L.nvrtcDestroyProgram(ctypes.byref(prog))
+    return rc, log.value.decode(errors="replace")
+
+
+def _units(p, dtype):
+    src = qf.qf_program_jit_source(p, dtype)
+    return [u for u in src.split("// ---- translation unit\n") if u.strip()]
+
+
+CASES = [
+    ("d3 random", 3, 9, lambda: W.random_circuit(3, 9, 40), qf.QF_C64, 0),
+    ("d2 random c128", 2, 12, lambda: W.random_circuit(2, 12, 40), qf.QF_C128, 0),
+    ("d5 random", 5, 5, lambda: W.random_circuit(5, 5, 30), qf.QF_C64, 0),
+    ("d4 slots 1", 4, 6, lambda: W.random_circuit(4, 6, 30), qf.QF_C64, 1),
+]
+
+
+@pytest.mark.parametrize("name,d,n,mk,dtype,slots", CASES, ids=[c[0] for c in CASES])
+def test_generated_passes_compile(name, d, n, mk, dtype, slots):
+    L = _nvrtc()
+    p = qf.program_from_ops(d, n, mk())
+    qf.qf_program_set_stage_slots(p, slots)
+    units = _units(p, dtype)
+    assert units
+    for u in units[:2]:
+        rc, log = _compile(L, u)
+        assert rc == 0, log[:2000]
+    qf.qf_program_free(p)
+
+
+def test_generated_special_ops_compile():
+    """SWAP and a two-qudit dense gate (shared-memory ops), controlled
+    rotations with the control outside the stage, a multi-controlled gate
+    (its own pass, no compiled source)."""
+    L = _nvrtc()
+    d, n = 3, 7
+    rng = np.random.default_rng(1)
+    ops = [W.Op("h", (q,)) for q in range(n)]
+    ops += [W.Op("swap", (1, 5)), W.Op("u", (2, 6), matrix=W.haar_unitary(9, rng)),
+            W.Op("crot", (0, 6), j=0, k=2, axis="x", theta=0.3), W.Op("crot", (6, 0), j=1, k=2, axis="z", theta=0.5),
+            W.Op("sum", (5, 6)), W.Op("sum", (6, 1)), W.Op("rot", (3,), j=2, axis="g", theta=0.2),
+            W.Op("mcx", (0, 1, 2)), W.Op("z", (4,), power=2), W.Op("x", (4,), power=1)]
+    p = qf.program_from_ops(d, n, ops)
+    units = _units(p, qf.QF_C64)
+    src = "".join(units)
+    assert "tile[e2]" in src and "offs[" in src     # SWAP and dense k-qudit code present
+    for u in units:
+        rc, log = _compile(L, u)
+        assert rc == 0, log[:2000]
+    qf.qf_program_free(p)
