@@ -212,10 +212,9 @@ qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev);
 
 /* Allocation-free <N_q> (no counterpart in the paper; a deployment aid).
  * For callers that cannot allocate device memory at the point of measurement
- * -- code being recorded into a CUDA graph, host callbacks and latency-bound
- * loops that must not trigger the device-wide synchronisation an allocation
- * or free can cause, and hosts whose own memory pool holds the whole device
- * heap.  Computes what qf_expect with QF_OBS_NUMBER_ALL computes:
+ * -- host callbacks and latency-bound loops that must not trigger the
+ * device-wide synchronisation an allocation or free can cause, and hosts
+ * whose own memory pool holds the whole device heap.  Computes what qf_expect with QF_OBS_NUMBER_ALL computes:
  * out_dev[q] = <N_q> for q < n and out_dev[n] = sum_i |psi_i|^2 (n + 1 FP64
  * values, device memory, 8-byte aligned), from the caller's d^n amplitudes at
  * psi_dev (device, 16-byte aligned, interleaved as dt), asynchronously on

@@ -318,10 +318,8 @@ template cudaError_t launch_fibre_reduce_g<double>(const Launch &, const cplx<do
 // Allocation-free <N_q> entry point.
 //
 // Some callers cannot allocate device memory when they need a measurement:
-// code recording a CUDA graph (an allocation inside stream capture breaks or
-// serialises the capture), host callbacks and latency-critical loops that must
-// not trigger the implicit device synchronisation cudaMalloc/cudaFree can
-// cause, and hosts whose framework owns the whole device heap through its own
+// host callbacks and latency-critical loops that must not trigger the
+// implicit device synchronisation cudaMalloc/cudaFree can cause, and hosts whose framework owns the whole device heap through its own
 // pool and leaves nothing for a library to take.  For them this entry point
 // reduces a caller-owned state into a caller-owned output and keeps the
 // per-CTA partial sums in a fixed file-scope device array instead of the

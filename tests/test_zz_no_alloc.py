@@ -1,8 +1,9 @@
 """The allocation-free <N_q> entry point (qf_expect_number_noalloc).
 
 It exists for callers that cannot allocate device memory when they measure
-(graph recording, host callbacks, hosts whose memory pool owns the device
-heap): it writes <N_q> and the norm for a caller-owned state into a
+(host callbacks and latency-bound loops that must not trigger the device-wide
+synchronisation an allocation can cause, hosts whose memory pool owns the
+device heap): it writes <N_q> and the norm for a caller-owned state into a
 caller-owned device buffer, keeping its partial sums in a fixed device array.
 Here it is called through the C ABI twice in a row -- the second time on a
 different state, so the shared scratch still holds the first call's partials
