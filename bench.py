@@ -138,7 +138,8 @@ class ClockSampler:
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("k_tile.cu", "tile_device.cuh", "qf_internal.cuh"):
+    # the fused passes run as tile kernels generated by qf_jit.cu
+    for f in ("qf_jit.cu", "qf_gates.cu", "qf_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2409_17716_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -314,7 +315,7 @@ def main():
     achieved = (tile_bytes / (tile_ms / 1e3)) / 1e9 if tile_ms > 0 else None
     ratio = traffic_ratio()
     avg_alg = tile_bytes / n_tile if n_tile else None
-    roofline = {"bound": "hbm", "kernel": "k_tile (fused pass)", "achieved": achieved, "peak": hbm_peak,
+    roofline = {"bound": "hbm", "kernel": "k_tile_jit (compiled fused pass)", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": (achieved / hbm_peak) if achieved else None,
                 "traffic": (ratio * avg_alg) if (ratio and avg_alg) else None,
                 "algorithmic_bytes_per_launch": avg_alg, "launches": n_tile,

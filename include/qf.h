@@ -286,8 +286,9 @@ qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, char *buf, size_t ca
 qf_status qf_program_set_fusion(qf_program *p, int enable);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
- * per shared-memory tile (capped by the default, d^t amplitudes <= 8192 for
- * complex64 / 4096 for complex128); min_run_qudits = lowest qudits always in
+ * per shared-memory tile (default: the largest t with d^t amplitudes <= 8192
+ * for complex64 / 4096 for complex128; a forward-pass override may go up to
+ * 160 KiB of amplitudes per tile); min_run_qudits = lowest qudits always in
  * the tile, so every contiguous run read from HBM has d^r amplitudes (default
  * 5, 3, 2, 1 for d = 2, 3, 4, 5, chosen by measurement; otherwise the smallest
  * r with d^r >= 32); max_ops = gates per pass (<= 96).  Takes

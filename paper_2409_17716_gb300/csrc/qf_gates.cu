@@ -379,6 +379,19 @@ int default_tile_qudits(int d, bool c128) {
     return nt;
 }
 
+// Largest tile an explicit override may ask for: d^nt amplitudes of at most
+// 160 KiB, leaving room in the 227 KiB of shared memory a CTA can hold.
+int max_tile_qudits(int d, bool c128) {
+    const long long cap = (160 * 1024) / (c128 ? 16 : 8);
+    int nt = 0;
+    long long t = 1;
+    while (t * d <= cap) {
+        t *= d;
+        ++nt;
+    }
+    return nt < kMaxTileQ ? nt : kMaxTileQ;
+}
+
 // Lowest qudits always kept in a tile, so every run a tile reads from HBM
 // is d^r contiguous amplitudes.  Longer runs read HBM more efficiently, shorter
 // ones leave room for more active qudits (more gates per pass).  Measured on
@@ -479,7 +492,9 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
                                   int nt_override, int max_ops, int rl_override) {
     std::vector<PassPlan> plan;
     int nt_max = std::min(default_tile_qudits(d, c128), kMaxTileQ);
-    if (nt_override > 0 && nt_override < nt_max) nt_max = nt_override;
+    // an override may exceed the default tile only in the forward (the
+    // adjoint holds two tiles, psi and lambda)
+    if (nt_override > 0) nt_max = std::min(nt_override, for_adjoint ? nt_max : max_tile_qudits(d, c128));
     const int op_cap = (max_ops > 0 && max_ops < kMaxTileOps) ? max_ops : kMaxTileOps;
     const int rl_min = std::min(rl_override > 0 ? rl_override : min_low_qudits(d), nt_max);
     std::vector<int> remaining(gates.size());

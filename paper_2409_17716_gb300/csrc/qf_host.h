@@ -175,6 +175,7 @@ struct PassPlan {
 };
 
 int default_tile_qudits(int d, bool c128);   // nt_max
+int max_tile_qudits(int d, bool c128);       // largest explicit override
 int min_low_qudits(int d);                   // rL_min (SEG >= 32)
 long long ipow_ll(int d, int e);
 
