@@ -148,7 +148,7 @@ def kernel_hash():
 def traffic_ratio():
     """DRAM bytes / algorithmic bytes of one tile-kernel launch from the
     committed ncu summary, or None if the kernel changed since."""
-    path = os.path.join(ROOT, "profiles", "k_tile_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_tile_jit_traffic.json")
     try:
         with open(path) as f:
             j = json.load(f)
