@@ -279,10 +279,11 @@ qf_status qf_program_set_jit(qf_program *p, int enable);
  * default for d, 4 for d = 2 and 2 for d = 3..5 in complex64): more slots
  * mean fewer shared-memory round trips and more registers per thread. */
 qf_status qf_program_set_stage_slots(qf_program *p, int slots);
-/* The CUDA source the program's tile passes compile from (for dtype dt), as
- * a NUL-terminated string of *len bytes; buf (capacity cap) may be NULL to
- * query the length.  Host only; nothing is compiled or launched. */
-qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, char *buf, size_t cap, size_t *len);
+/* The CUDA source the program's tile passes compile from (for dtype dt; the
+ * forward passes, or with adjoint != 0 the reverse passes of the adjoint
+ * sweep), as a NUL-terminated string of *len bytes; buf (capacity cap) may be
+ * NULL to query the length.  Host only; nothing is compiled or launched. */
+qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, int adjoint, char *buf, size_t cap, size_t *len);
 qf_status qf_program_set_fusion(qf_program *p, int enable);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits

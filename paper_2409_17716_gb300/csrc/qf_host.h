@@ -202,10 +202,14 @@ qf_status program_gates(const qf_program *p, std::vector<HGate> *out);
 // Tile passes of a program compiled at plan time (qf_jit.cu).
 struct JitProgram;
 qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                    int k_override, int num_sms, JitProgram **out);
+                    int k_override, bool adj, int num_sms, JitProgram **out);
+qf_status jit_launch_adj(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, void *lam, double *rows,
+                         const TileGeom &g, const void *prepared, int npool, const void *gpool);
+int jit_pass_grid(const JitProgram *jp, size_t pi);
+int jit_pass_ncols(const JitProgram *jp, size_t pi);
 void jit_free(JitProgram *jp);
 qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                     int k_override, std::string *out);
+                     int k_override, bool adj, std::string *out);
 bool jit_pass_ready(const JitProgram *jp, size_t pi);
 bool jit_pass_global_pool(const JitProgram *jp, size_t pi);
 qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,

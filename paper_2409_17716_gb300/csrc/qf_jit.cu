@@ -170,6 +170,8 @@ struct PassSrc {
     int d, T, SEG, nt, kA, nruns, K, threads;
     bool c128, params;   // params: entries in the kernel parameters, else global
     int npool;
+    bool adj = false;    // reverse pass of the adjoint sweep (psi and lambda, gradient columns)
+    int ncols = 0;       // gradient columns (parametrised ops, op.gcol) of an adjoint pass
     std::vector<TOp> ops;
     std::vector<TStage> stages;
 };
@@ -217,6 +219,71 @@ class Gen {
         o_ << "    __syncthreads();\n  }\n}\n";
     }
 
+    // Reverse pass of the adjoint sweep: psi and lambda tiles; every op is
+    // U^+ (entries at op.mat); a parametrised op first adds Im <lambda|G|psi>
+    // of the block (generator entries at op.gmat) to its column; each CTA
+    // writes one row of 2 x column sums.
+    void kernel_adj(const std::string &name) {
+        const int NG = std::max(1, 2 * p_.nruns + p_.kA);
+        const int NP = std::max(1, p_.params ? p_.npool : 1);
+        const int NA = p_.T / p_.SEG;
+        const int WARPS = p_.threads / 32;
+        const int NC = p_.ncols;
+        o_ << "struct __align__(16) A_" << name << " { C *psi; C *lam; const P *gp; double *rows; long long ntiles; "
+           << "long long geo[" << NG << "]; P pool[" << NP << "]; };\n";
+        o_ << "extern \"C\" __global__ void __launch_bounds__(" << p_.threads << ") " << name
+           << "(const __grid_constant__ A_" << name << " A) {\n";
+        o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
+        o_ << "  __shared__ long long qj_base;\n";
+        o_ << "  __shared__ double qj_red[" << std::max(1, NC * WARPS) << "];\n";
+        o_ << "  C *tile = reinterpret_cast<C *>(qj_sm);\n";
+        o_ << "  C *ltile = tile + " << p_.T << ";\n";
+        o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm + " << (size_t)2 * p_.T * elt() << ");\n";
+        o_ << "  const int tid = threadIdx.x;\n";
+        for (int c = 0; c < NC; ++c) o_ << "  double g" << c << " = 0.0;\n";
+        o_ << "  for (int a = tid; a < " << NA << "; a += " << p_.threads << ") {\n    long long o = 0; int rem = a;\n";
+        for (int i = p_.kA - 1; i >= 0; --i)
+            o_ << "    o += (long long)(rem % " << D_ << ") * A.geo[" << 2 * p_.nruns + i << "]; rem /= " << D_ << ";\n";
+        o_ << "    offA[a] = o;\n  }\n";
+        o_ << "  if (tid == 0) qj_base = qj_tile_base_" << name << "(A, blockIdx.x);\n";
+        o_ << "  __syncthreads();\n";
+        o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
+        o_ << "    const long long base = qj_base;\n";
+        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
+           << "; const long long gi = base + offA[a] + (e - a * " << p_.SEG
+           << "); qj_cp(tile + e, A.psi + gi); qj_cp(ltile + e, A.lam + gi); }\n";
+        o_ << "    qj_wait();\n    __syncthreads();\n";
+        for (const TStage &st : p_.stages) {
+            if (st.legacy) {
+                tn_ = "tile";
+                legacy(p_.ops[st.first]);
+                tn_ = "ltile";
+                legacy(p_.ops[st.first]);
+                tn_ = "tile";
+            } else {
+                stage_adj(st);
+            }
+            o_ << "    __syncthreads();\n";
+        }
+        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
+           << "; const long long gi = base + offA[a] + (e - a * " << p_.SEG
+           << "); A.psi[gi] = tile[e]; A.lam[gi] = ltile[e]; }\n";
+        o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
+           << "(A, t + gridDim.x);\n";
+        o_ << "    __syncthreads();\n  }\n";
+        if (NC > 0) {
+            o_ << "  const int lane = tid & 31, wid = tid >> 5;\n";
+            for (int c = 0; c < NC; ++c)
+                o_ << "  { double x = g" << c << "; for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);"
+                   << " if (lane == 0) qj_red[" << c * WARPS << " + wid] = x; }\n";
+            o_ << "  __syncthreads();\n";
+            o_ << "  for (int c = tid; c < " << NC << "; c += " << p_.threads << ") { double s = 0.0; for (int w = 0; w < "
+               << WARPS << "; ++w) s += qj_red[c * " << WARPS << " + w]; A.rows[(long long)blockIdx.x * " << NC
+               << " + c] = 2.0 * s; }\n";
+        }
+        o_ << "}\n";
+    }
+
     void tile_base_fn(const std::string &name) {
         o_ << "struct A_" << name << ";\n";
         o_ << "template <typename AT> __device__ __forceinline__ long long qj_tile_base_" << name
@@ -234,9 +301,14 @@ class Gen {
     std::ostringstream &o_;
     int D_;
 
+    std::string vp_ = "v";       // register block the ops write (v: psi, w: lambda)
+    std::string tn_ = "tile";    // shared-memory tile of legacy ops
+
     std::string E(int k) const { return (p_.params ? "A.pool[" : "A.gp[") + std::to_string(k) + "]"; }
     std::string Edyn(const std::string &expr) const { return (p_.params ? "A.pool[" : "A.gp[") + expr + "]"; }
-    static std::string V(int r) { return "v" + std::to_string(r); }
+    std::string V(int r) const { return vp_ + std::to_string(r); }
+    static std::string W(int r) { return "w" + std::to_string(r); }
+    static std::string Pv(int r) { return "v" + std::to_string(r); }
 
     // ---------------------------------------------------------------- register stage
     void stage(const TStage &st) {
@@ -255,6 +327,114 @@ class Gen {
         for (int i = 0; i < st.nops; ++i) op(p_.ops[st.first + i]);
         for (int r = 0; r < DK; ++r) o_ << "      tile[b + " << off[r] << "] = " << V(r) << ";\n";
         o_ << "    }\n";
+    }
+
+    void stage_adj(const TStage &st) {
+        const int K = p_.K, DK = ipow_i(D_, K), NBLK = p_.T / DK;
+        o_ << "    for (int blk = tid; blk < " << NBLK << "; blk += " << p_.threads << ") {\n      int b = blk;\n";
+        for (int i = 0; i < K; ++i)
+            o_ << "      { const int q = b / " << st.lsa[i] << "; b = q * " << st.lsa[i] * D_ << " + (b - q * "
+               << st.lsa[i] << "); }\n";
+        std::vector<int> off(DK);
+        for (int r = 0; r < DK; ++r) {
+            int o = 0;
+            for (int i = 0; i < K; ++i) o += ((r / ipow_i(D_, K - 1 - i)) % D_) * st.ls[i];
+            off[r] = o;
+        }
+        for (int r = 0; r < DK; ++r)
+            o_ << "      C " << Pv(r) << " = tile[b + " << off[r] << "]; C " << W(r) << " = ltile[b + " << off[r] << "];\n";
+        for (int i = 0; i < st.nops; ++i) {
+            const TOp &o = p_.ops[st.first + i];
+            if (o.gcol >= 0) grad(o);
+            vp_ = "v";
+            op(o);
+            vp_ = "w";
+            op(o);
+            vp_ = "v";
+        }
+        for (int r = 0; r < DK; ++r)
+            o_ << "      tile[b + " << off[r] << "] = " << Pv(r) << "; ltile[b + " << off[r] << "] = " << W(r) << ";\n";
+        o_ << "    }\n";
+    }
+
+    // Im(conj(lambda) * x) for register names.
+    static std::string imc(const std::string &l, const std::string &x) {
+        return "(" + l + ".x * " + x + ".y - " + l + ".y * " + x + ".x)";
+    }
+
+    // Adds the block's Im <lambda|G|psi> of a parametrised op to g<gcol>.
+    void grad(const TOp &o) {
+        const int sa = o.q[4], sc = o.q[5];
+        const int gm = o.gmat;
+        const bool ctrl = is_controlled(o);
+        const std::string gv = "g" + std::to_string(o.gcol);
+        if (o.kind == OP_PAIR || o.kind == OP_CPAIR) {
+            const int RS = rs(sa);
+            auto fib = [&](int b0, const std::string &scale) {
+                const std::string a = Pv(b0 + o.j * RS), c = Pv(b0 + o.k * RS);
+                const std::string la = W(b0 + o.j * RS), lc = W(b0 + o.k * RS);
+                o_ << "      { const C ga = jma(" << E(gm + 1) << ", " << c << ", jm(" << E(gm) << ", " << a
+                   << ")); const C gc = jma(" << E(gm + 3) << ", " << c << ", jm(" << E(gm + 2) << ", " << a << ")); "
+                   << "qt += " << scale << "(" << imc(la, "ga") << " + " << imc(lc, "gc") << "); }\n";
+            };
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { decltype(C().x) qt = 0;\n";
+                for (int b0 : fibres(sa)) fib(b0, "");
+                o_ << "      " << gv << " += (double)qt * cl; } }\n";
+                return;
+            }
+            o_ << "      { decltype(C().x) qt = 0;\n";
+            for (int b0 : fibres(sa)) {
+                if (ctrl) {
+                    const int cl = slot_digit(b0, sc);
+                    if (cl == 0) continue;
+                    fib(b0, std::to_string(cl) + " * ");
+                } else {
+                    fib(b0, "");
+                }
+            }
+            o_ << "      " << gv << " += (double)qt; }\n";
+            return;
+        }
+        if (o.kind == OP_DIAG || o.kind == OP_CDIAG) {
+            if (sa < 0) {
+                const int DK = ipow_i(D_, p_.K);
+                o_ << "      { const int dg = " << outside_digit(o.lsa) << "; if ((" << o.mask
+                   << " >> dg) & 1) { decltype(C().x) qt = 0;";
+                for (int r = 0; r < DK; ++r) o_ << " qt += " << imc(W(r), Pv(r)) << ";";
+                o_ << " " << gv << " += (double)(" << Edyn(std::to_string(gm) + " + dg") << ".x * qt); } }\n";
+                return;
+            }
+            const int RS = rs(sa);
+            auto fib = [&](int b0, const std::string &scale) {
+                o_ << "      qt += " << scale << "(";
+                bool first = true;
+                for (int l = 0; l < D_; ++l)
+                    if ((o.mask >> l) & 1) {
+                        o_ << (first ? "" : " + ") << E(gm + l) << ".x * " << imc(W(b0 + l * RS), Pv(b0 + l * RS));
+                        first = false;
+                    }
+                if (first) o_ << "0";
+                o_ << ");\n";
+            };
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { decltype(C().x) qt = 0;\n";
+                for (int b0 : fibres(sa)) fib(b0, "");
+                o_ << "      " << gv << " += (double)qt * cl; } }\n";
+                return;
+            }
+            o_ << "      { decltype(C().x) qt = 0;\n";
+            for (int b0 : fibres(sa)) {
+                if (ctrl) {
+                    const int cl = slot_digit(b0, sc);
+                    if (cl == 0) continue;
+                    fib(b0, std::to_string(cl) + " * ");
+                } else {
+                    fib(b0, "");
+                }
+            }
+            o_ << "      " << gv << " += (double)qt; }\n";
+        }
     }
 
     int rs(int S) const { return ipow_i(D_, p_.K - 1 - S); }
@@ -400,8 +580,8 @@ class Gen {
             const int la = o.lsa, lc = o.lsc;
             o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") {\n";
             o_ << "      const int x = (e / " << la << ") % " << D_ << ", y = (e / " << lc << ") % " << D_ << ";\n";
-            o_ << "      if (x < y) { const int e2 = e + (y - x) * " << (la - lc)
-               << "; const C t0 = tile[e]; tile[e] = tile[e2]; tile[e2] = t0; }\n    }\n";
+            o_ << "      if (x < y) { const int e2 = e + (y - x) * " << (la - lc) << "; const C t0 = " << tn_ << "[e]; "
+               << tn_ << "[e] = " << tn_ << "[e2]; " << tn_ << "[e2] = t0; }\n    }\n";
             return;
         }
         // OP_DENSEK: entries always in global memory (up to 64 x 64)
@@ -423,10 +603,10 @@ class Gen {
             o_ << (r ? ", " : "") << off;
         }
         o_ << "};\n      C xs[" << DK << "];\n";
-        o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = tile[b + offs[r]];\n";
+        o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = " << tn_ << "[b + offs[r]];\n";
         o_ << "      for (int r = 0; r < " << DK << "; ++r) { C acc = jm(A.gp[" << o.mat << " + r * " << DK
            << "], xs[0]); for (int x = 1; x < " << DK << "; ++x) acc = jma(A.gp[" << o.mat << " + r * " << DK
-           << " + x], xs[x], acc); tile[b + offs[r]] = acc; }\n    }\n";
+           << " + x], xs[x], acc); " << tn_ << "[b + offs[r]] = acc; }\n    }\n";
     }
 };
 
@@ -435,12 +615,21 @@ std::string cuda_err(CUresult r) { return "CUresult " + std::to_string((int)r); 
 }  // namespace
 
 // Register slots of a generated register stage.
+// Register slots of a generated reverse (adjoint) stage: psi and lambda
+// blocks both live in registers.
+int jit_stage_k_adj(int d, bool c128) {
+    if (c128) return d == 2 ? 2 : 1;
+    return d == 2 ? 3 : d <= 4 ? 2 : 1;
+}
+
 int jit_stage_k(int d, bool c128) {
     if (c128) return d == 2 ? 3 : (d == 3 || d == 4) ? 2 : 1;
     return d == 2 ? 4 : d <= 5 ? 2 : 1;
 }
 
 struct JitPassInfo {
+    int ncols = 0;          // gradient columns (adjoint passes)
+    size_t header = 24;     // bytes of pointers and tile count before geo[]
     CUfunction fn = nullptr;
     int threads = 256;
     size_t smem = 0;
@@ -460,7 +649,7 @@ struct JitProgram {
 // `ops` are the passes' localized ops in pool order (op.mat already set), one
 // vector per pass; k_override > 0 sets the register slots per stage.
 static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops,
-                                            int d, bool c128, int k_override, JitProgram *jp,
+                                            int d, bool c128, int k_override, bool adj, JitProgram *jp,
                                             std::vector<std::string> &names) {
     jp->passes.resize(plan.size());
     names.assign(plan.size(), std::string());
@@ -477,7 +666,8 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.nt = pp.geom.nt;
         ps.kA = pp.geom.kA;
         ps.nruns = pp.geom.nruns;
-        ps.K = std::min(k_override > 0 ? k_override : jit_stage_k(d, c128), pp.geom.nt);
+        ps.adj = adj;
+        ps.K = std::min(k_override > 0 ? k_override : (adj ? jit_stage_k_adj(d, c128) : jit_stage_k(d, c128)), pp.geom.nt);
         ps.ops = ops[pi];
         ps.stages = build_stages(ps.ops, pp.geom, d, ps.K);
         ops[pi] = ps.ops;   // the stage slots written by build_stages
@@ -497,37 +687,45 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
             default: cnt = 0;
             }
             npool = std::max(npool, o.mat + cnt);
+            if (adj && o.gcol >= 0) {
+                const int gcnt = (o.kind == OP_PAIR || o.kind == OP_CPAIR) ? 4 : d;
+                npool = std::max(npool, o.gmat + gcnt);
+                ps.ncols = std::max(ps.ncols, o.gcol + 1);
+            }
         }
         ps.npool = npool;
         ps.params = npool <= kParamPoolMax && !dense_k;
         const int DK = ipow_i(d, ps.K);
         ps.threads = (ps.T / DK <= 128) ? 128 : 256;
         std::ostringstream nm;
-        nm << "k_tile_jit_d" << d << (c128 ? "_c128_" : "_c64_") << pi;
+        nm << (adj ? "k_tile_adj_jit_d" : "k_tile_jit_d") << d << (c128 ? "_c128_" : "_c64_") << pi;
         names[pi] = nm.str();
         std::ostringstream src;
         src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n" << kPrelude;
         Gen g(ps, src);
         g.tile_base_fn(names[pi]);
-        g.kernel(names[pi]);
+        if (adj) g.kernel_adj(names[pi]);
+        else g.kernel(names[pi]);
         out[pi] = src.str();
         JitPassInfo &ji = jp->passes[pi];
         ji.threads = ps.threads;
-        ji.smem = (size_t)ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;
+        ji.smem = (size_t)(adj ? 2 : 1) * ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;
+        ji.ncols = ps.ncols;
+        ji.header = adj ? 40 : 24;
         ji.params = ps.params;
         ji.npool = npool;
         ji.NG = std::max(1, 2 * ps.nruns + ps.kA);
-        ji.pool_off = (24 + 8 * (size_t)ji.NG + 15) & ~(size_t)15;
+        ji.pool_off = (ji.header + 8 * (size_t)ji.NG + 15) & ~(size_t)15;
         ji.arg_bytes = ji.pool_off + 16 * (size_t)std::max(1, ps.params ? npool : 1);
     }
     return out;
 }
 
 qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                     int k_override, std::string *out) {
+                     int k_override, bool adj, std::string *out) {
     JitProgram jp;
     std::vector<std::string> names;
-    std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, &jp, names);
+    std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, &jp, names);
     out->clear();
     for (const std::string &x : srcs)
         if (!x.empty()) *out += "// ---- translation unit\n" + x;
@@ -613,12 +811,12 @@ bool nvrtc_compile(const std::string &code, const std::string &arch, std::vector
 // of this process first, then cubins cached on disk, then NVRTC (passes
 // compiled in parallel threads).
 qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                    int k_override, int num_sms, JitProgram **out) {
+                    int k_override, bool adj, int num_sms, JitProgram **out) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!load_apis()) return set_error(QF_ERR_UNSUPPORTED, g_load_err);
     JitProgram *jp = new JitProgram();
     std::vector<std::string> names;
-    const std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, jp, names);
+    const std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, jp, names);
     int major = 10, minor = 3, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -716,5 +914,34 @@ qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void 
     if (r != CUDA_SUCCESS) return set_error(QF_ERR_CUDA, "tile pass launch failed: " + cuda_err(r));
     return QF_OK;
 }
+
+// Launches reverse pass pi of the adjoint sweep; rows receives grid x ncols
+// doubles (jit_pass_grid, jit_pass_ncols).
+qf_status jit_launch_adj(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, void *lam, double *rows,
+                         const TileGeom &g, const void *prepared, int npool, const void *gpool) {
+    const JitPassInfo &ji = jp->passes[pi];
+    std::vector<unsigned char> args(ji.arg_bytes, 0);
+    std::memcpy(args.data(), &psi, 8);
+    std::memcpy(args.data() + 8, &lam, 8);
+    std::memcpy(args.data() + 16, &gpool, 8);
+    std::memcpy(args.data() + 24, &rows, 8);
+    std::memcpy(args.data() + 32, &g.ntiles, 8);
+    long long geo[2 * (kMaxActive + 1) + kMaxActive] = {};
+    for (int r = 0; r < g.nruns; ++r) {
+        geo[r] = g.runM[r];
+        geo[g.nruns + r] = g.runS[r];
+    }
+    for (int i = 0; i < g.kA; ++i) geo[2 * g.nruns + i] = g.strideA[i];
+    std::memcpy(args.data() + 40, geo, 8 * (size_t)(2 * g.nruns + g.kA));
+    if (ji.params && npool > 0) std::memcpy(args.data() + ji.pool_off, prepared, 16 * (size_t)npool);
+    void *kp[] = {args.data()};
+    const CUresult r = g_drv.launch(ji.fn, (unsigned)ji.grid, 1, 1, (unsigned)ji.threads, 1, 1, (unsigned)ji.smem,
+                                    (CUstream)stream, kp, nullptr);
+    if (r != CUDA_SUCCESS) return set_error(QF_ERR_CUDA, "adjoint tile pass launch failed: " + cuda_err(r));
+    return QF_OK;
+}
+
+int jit_pass_grid(const JitProgram *jp, size_t pi) { return jp->passes[pi].grid; }
+int jit_pass_ncols(const JitProgram *jp, size_t pi) { return jp->passes[pi].ncols; }
 
 }  // namespace qf

@@ -7,6 +7,7 @@
 // the op lists and matrix pools of all passes in one copy, and launches the
 // passes in order on the state's stream.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 
@@ -26,6 +27,8 @@ struct qf_program {
     int jit_k = 0;                     // register slots per compiled stage (0: default per d)
     JitProgram *jitp = nullptr;        // compiled passes of `plan` (nullptr: not built)
     bool jit_c128 = false;
+    JitProgram *jitadj = nullptr;      // compiled reverse passes of `adj_plan`
+    bool jitadj_c128 = false;
     int tile_qudits = 0, min_run_qudits = 0, max_ops = 0;   // planner overrides (0: default)
     bool plan_valid = false;
     bool plan_c128 = false;
@@ -183,6 +186,10 @@ static void drop_jit(qf_program *p) {
         jit_free(p->jitp);
         p->jitp = nullptr;
     }
+    if (p->jitadj) {
+        jit_free(p->jitadj);
+        p->jitadj = nullptr;
+    }
 }
 
 // Localized ops of every tile pass in pool order (entries at `params`).
@@ -212,7 +219,7 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
     if (!p->jitp || p->jit_c128 != c128) {
         drop_jit(p);
         std::vector<std::vector<TOp>> ops = jit_ops(p, params);
-        qf_status st = jit_build(p->plan, ops, d, c128, p->jit_k, s->num_sms, &p->jitp);
+        qf_status st = jit_build(p->plan, ops, d, c128, p->jit_k, false, s->num_sms, &p->jitp);
         if (st != QF_OK) return st;
         p->jit_c128 = c128;
     }
@@ -420,6 +427,164 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
     return QF_OK;
 }
 
+// Reverse passes in execution order (last planned pass first) and, per
+// tile pass, its ops in application order: U^+ entries at op.mat and, for a
+// parametrised op, its generator entries at op.gmat with gradient column
+// op.gcol.  With `prep`, also the prepared entries of every pass.
+template <typename R>
+static std::vector<std::vector<TOp>> adj_jit_ops(const qf_program *p, const std::vector<PassPlan> &exec,
+                                                 const double *params, std::vector<std::vector<unsigned char>> *prep) {
+    std::vector<std::vector<TOp>> ops(exec.size());
+    if (prep) prep->assign(exec.size(), std::vector<unsigned char>());
+    for (size_t k = 0; k < exec.size(); ++k) {
+        const PassPlan &pp = exec[k];
+        if (pp.strided || pp.mc) continue;
+        int off = 0, ncols = 0;
+        for (int gi = (int)pp.groups.size() - 1; gi >= 0; --gi) {
+            const auto &grp = pp.groups[gi];
+            ROp r = dagger(resolve_group(p->gates, grp, p->d, params), p->d);
+            TOp o = localize(r.op, pp.geom, pp.active, p->n, p->d);
+            o.mat = off;
+            off += (int)r.m.size();
+            if (prep) append_prepared<R>(r, (*prep)[k]);
+            o.gcol = -1;
+            o.gmat = 0;
+            const HGate &g0 = p->gates[grp[0]];
+            if (grp.size() == 1 && gate_is_param(g0)) {
+                o.gcol = ncols++;
+                o.gmat = off;
+                ROp gen;
+                gen.m = generator_entries(g0, p->d);
+                off += (int)gen.m.size();
+                if (prep) append_prepared<R>(gen, (*prep)[k]);
+            }
+            ops[k].push_back(o);
+        }
+    }
+    return ops;
+}
+
+// Adjoint sweep with compiled reverse passes (same plan, gradient rows and
+// gather as the generic sweep below).
+template <typename R>
+static qf_status run_adjoint_jit(qf_program *p, qf_state *psi, qf_state *lam, const double *params,
+                                 const double *weights, double *loss_dev, double *grad_dev) {
+    using C = cplx<R>;
+    const int d = p->d, n = p->n;
+    const bool c128 = sizeof(R) == 8;
+    const int np = (int)p->adj_plan.size();
+    std::vector<PassPlan> exec(p->adj_plan.rbegin(), p->adj_plan.rend());
+    if (!p->jitadj || p->jitadj_c128 != c128) {
+        if (p->jitadj) {
+            jit_free(p->jitadj);
+            p->jitadj = nullptr;
+        }
+        std::vector<std::vector<TOp>> ops = adj_jit_ops<R>(p, exec, params, nullptr);
+        qf_status st = jit_build(exec, ops, d, c128, p->jit_k, true, psi->num_sms, &p->jitadj);
+        if (st != QF_OK) return st;
+        p->jitadj_c128 = c128;
+    }
+    std::vector<std::vector<unsigned char>> prep;
+    adj_jit_ops<R>(p, exec, params, &prep);
+    // gradient rows and terms: (rows base, CTAs, columns, column) per slot, in execution order
+    std::vector<long long> rows_base(np, 0);
+    std::vector<std::vector<std::array<long long, 4>>> terms(p->num_params);
+    long long rows_total = 0;
+    std::vector<ROp> single(np);
+    for (int k = 0; k < np; ++k) {
+        const PassPlan &pp = exec[k];
+        if (pp.strided || pp.mc) {
+            single[k] = dagger(resolve_group(p->gates, pp.groups[0], d, params), d);
+            continue;
+        }
+        const int grid = jit_pass_grid(p->jitadj, k), nc = jit_pass_ncols(p->jitadj, k);
+        rows_base[k] = rows_total;
+        rows_total += (long long)grid * nc;
+        int col = 0;
+        for (int gi = (int)pp.groups.size() - 1; gi >= 0; --gi) {
+            const auto &grp = pp.groups[gi];
+            const HGate &g0 = p->gates[grp[0]];
+            if (grp.size() == 1 && gate_is_param(g0)) terms[g0.slot].push_back({rows_base[k], grid, nc, col++});
+        }
+    }
+    std::vector<unsigned char> host;
+    std::vector<size_t> goff(np, 0);
+    for (int k = 0; k < np; ++k)
+        if (!exec[k].strided && !exec[k].mc && jit_pass_global_pool(p->jitadj, k)) {
+            goff[k] = align16(host.size());
+            host.resize(goff[k] + prep[k].size());
+            std::memcpy(host.data() + goff[k], prep[k].data(), prep[k].size());
+        }
+    const size_t tb = gather_term_bytes();
+    const size_t terms_off = align16(host.size());
+    std::vector<int> first(p->num_params + 1, 0);
+    host.resize(terms_off);
+    for (int sl = 0; sl < p->num_params; ++sl) {
+        first[sl + 1] = first[sl] + (int)terms[sl].size();
+        for (auto &t : terms[sl]) {
+            struct {
+                long long base;
+                int nrows, ncols, col, pad;
+            } rec = {t[0], (int)t[1], (int)t[2], (int)t[3], 0};
+            static_assert(sizeof(rec) == 24, "gather term layout");
+            const size_t at = host.size();
+            host.resize(at + tb);
+            std::memcpy(host.data() + at, &rec, sizeof(rec));
+        }
+    }
+    const size_t first_off = align16(host.size());
+    host.resize(first_off + first.size() * sizeof(int));
+    std::memcpy(host.data() + first_off, first.data(), first.size() * sizeof(int));
+    if ((size_t)rows_total > p->rows_cap) {
+        if (p->ran) QF_CUDA(cudaEventSynchronize(p->done_ev));
+        if (p->d_rows) cudaFree(p->d_rows);
+        p->d_rows = nullptr;
+        p->rows_cap = 0;
+        size_t cap = (size_t)rows_total + 1024;
+        if (cudaMalloc(&p->d_rows, cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_OOM, "gradient scratch allocation failed");
+        }
+        p->rows_cap = cap;
+    }
+    qf_status st = upload(p, psi, host);
+    if (st != QF_OK) return st;
+    Launch L;
+    L.stream = psi->stream;
+    L.num_sms = psi->num_sms;
+    C *ps = reinterpret_cast<C *>(psi->data);
+    C *ls = reinterpret_cast<C *>(lam->data);
+    cudaError_t e = launch_number_obs<R>(L, ps, ls, d, n, weights, psi->d_partials, loss_dev);
+    if (e != cudaSuccess) return cuda_error(e, "lambda = O psi");
+    const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
+    const MixedShape ushape = uniform_shape(d, n);
+    for (int k = 0; k < np; ++k) {
+        const PassPlan &pp = exec[k];
+        if (pp.mc) {
+            const ROp &r = single[k];
+            std::vector<C> m(r.m.size());
+            for (size_t i = 0; i < m.size(); ++i) m[i] = mk<R>((R)r.m[i].real(), (R)r.m[i].imag());
+            if (!(r.op.kind == OP_MCSHIFT && r.op.s == 0)) {
+                e = launch_mc<R>(L, ps, ushape, r.op, m.data(), (int)m.size());
+                if (e == cudaSuccess) e = launch_mc<R>(L, ls, ushape, r.op, m.data(), (int)m.size());
+                if (e != cudaSuccess) return cuda_error(e, "adjoint multi-controlled gate");
+            }
+            continue;
+        }
+        const void *gp = jit_pass_global_pool(p->jitadj, k) ? (const void *)(dev + goff[k]) : nullptr;
+        st = jit_launch_adj(p->jitadj, k, psi->stream, ps, ls, p->d_rows + rows_base[k], pp.geom, prep[k].data(),
+                            (int)(prep[k].size() / 16), gp);
+        if (st != QF_OK) return st;
+    }
+    e = launch_grad_gather(L, p->d_rows, dev + terms_off, reinterpret_cast<const int *>(dev + first_off), p->num_params,
+                           grad_dev);
+    if (e != cudaSuccess) return cuda_error(e, "gradient gather");
+    QF_CUDA(cudaEventRecord(p->done_ev, psi->stream));
+    p->ran = true;
+    p->last_passes = np;
+    return QF_OK;
+}
+
 template <typename R>
 static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, const double *params, const double *weights,
                                double *loss_dev, double *grad_dev) {
@@ -430,7 +595,12 @@ static qf_status run_adjoint_t(qf_program *p, qf_state *psi, qf_state *lam, cons
         p->adj_plan = plan_passes(p->gates, d, n, c128, p->fuse, true, p->tile_qudits, p->max_ops, p->min_run_qudits);
         p->adj_valid = true;
         p->adj_c128 = c128;
+        if (p->jitadj) {
+            jit_free(p->jitadj);
+            p->jitadj = nullptr;
+        }
     }
+    if (p->jit) return run_adjoint_jit<R>(p, psi, lam, params, weights, loss_dev, grad_dev);
     const auto &plan = p->adj_plan;
     const int np = (int)plan.size();
     struct Built {
@@ -925,20 +1095,39 @@ qf_status qf_program_set_tiling(qf_program *p, int tile_qudits, int min_run_qudi
     return QF_OK;
 }
 
-qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, char *buf, size_t cap, size_t *len) {
+qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, int adjoint, char *buf, size_t cap, size_t *len) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     if (p->mixed) return set_error(QF_ERR_UNSUPPORTED, "mixed-dimension programs run gate by gate");
     const bool c128 = dt == QF_C128;
-    if (!p->plan_valid || p->plan_c128 != c128) {
-        p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops, p->min_run_qudits);
-        p->plan_valid = true;
-        p->plan_c128 = c128;
-        drop_jit(p);
-    }
     std::vector<double> zeros((size_t)std::max(1, p->num_params), 0.0);
-    std::vector<std::vector<TOp>> ops = jit_ops(p, zeros.data());
     std::string src;
-    qf_status st = jit_source(p->plan, ops, p->d, c128, p->jit_k, &src);
+    qf_status st;
+    if (adjoint) {
+        if (!p->adj_valid || p->adj_c128 != c128) {
+            p->adj_plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, true, p->tile_qudits, p->max_ops,
+                                      p->min_run_qudits);
+            p->adj_valid = true;
+            p->adj_c128 = c128;
+            if (p->jitadj) {
+                jit_free(p->jitadj);
+                p->jitadj = nullptr;
+            }
+        }
+        std::vector<PassPlan> exec(p->adj_plan.rbegin(), p->adj_plan.rend());
+        std::vector<std::vector<TOp>> ops = c128 ? adj_jit_ops<double>(p, exec, zeros.data(), nullptr)
+                                                 : adj_jit_ops<float>(p, exec, zeros.data(), nullptr);
+        st = jit_source(exec, ops, p->d, c128, p->jit_k, true, &src);
+    } else {
+        if (!p->plan_valid || p->plan_c128 != c128) {
+            p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops,
+                                  p->min_run_qudits);
+            p->plan_valid = true;
+            p->plan_c128 = c128;
+            drop_jit(p);
+        }
+        std::vector<std::vector<TOp>> ops = jit_ops(p, zeros.data());
+        st = jit_source(p->plan, ops, p->d, c128, p->jit_k, false, &src);
+    }
     if (st != QF_OK) return st;
     if (len) *len = src.size() + 1;
     if (buf && cap > 0) {

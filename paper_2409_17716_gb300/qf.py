@@ -85,7 +85,7 @@ _PROTOS = {
     "qf_program_set_fusion": (_int, [_vp, _int]),
     "qf_program_set_jit": (_int, [_vp, _int]),
     "qf_program_set_stage_slots": (_int, [_vp, _int]),
-    "qf_program_jit_source": (_int, [_vp, _int, _c.c_char_p, _c.c_size_t, _c.POINTER(_c.c_size_t)]),
+    "qf_program_jit_source": (_int, [_vp, _int, _int, _c.c_char_p, _c.c_size_t, _c.POINTER(_c.c_size_t)]),
     "qf_program_set_tiling": (_int, [_vp, _int, _int, _int]),
     "qf_program_run": (_int, [_vp, _vp, _c.POINTER(_dbl)]),
     "qf_program_last_passes": (_int, [_vp]),
@@ -449,12 +449,14 @@ def qf_program_set_stage_slots(p: int, slots: int = 0) -> None:
     _call("qf_program_set_stage_slots", p, int(slots))
 
 
-def qf_program_jit_source(p: int, dtype: int = QF_C64) -> str:
-    """CUDA source of the program's compiled tile passes."""
+def qf_program_jit_source(p: int, dtype: int = QF_C64, adjoint: bool = False) -> str:
+    """CUDA source of the program's compiled tile passes (forward, or the
+    reverse passes of the adjoint sweep)."""
     n = _c.c_size_t()
-    _call("qf_program_jit_source", p, dtype, None, 0, _c.byref(n))
+    a = 1 if adjoint else 0
+    _call("qf_program_jit_source", p, dtype, a, None, 0, _c.byref(n))
     buf = _c.create_string_buffer(n.value)
-    _call("qf_program_jit_source", p, dtype, buf, n.value, _c.byref(n))
+    _call("qf_program_jit_source", p, dtype, a, buf, n.value, _c.byref(n))
     return buf.value.decode()
 
 

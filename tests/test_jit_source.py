@@ -79,3 +79,23 @@ def test_generated_special_ops_compile():
         rc, log = _compile(L, u)
         assert rc == 0, log[:2000]
     qf.qf_program_free(p)
+
+
+@pytest.mark.parametrize("d,n,dtype", [(3, 8, qf.QF_C64), (2, 10, qf.QF_C128), (5, 4, qf.QF_C64)])
+def test_generated_adjoint_passes_compile(d, n, dtype):
+    """Reverse passes of the adjoint sweep: psi and lambda register blocks,
+    gradient terms of rotations and controlled rotations (controls inside
+    and outside a stage), shared-memory SWAP on both tiles."""
+    L = _nvrtc()
+    ops, P = W.variational_ansatz(d, n, 2)
+    ops = ops + [W.Op("crot", (0, n - 1), j=0, k=1, axis="y", param=0),
+                 W.Op("crot", (n - 1, 1), j=0, k=1, axis="z", param=1), W.Op("swap", (1, 2)),
+                 W.Op("rot", (2,), j=d - 1, axis="g", param=2)]
+    p = qf.program_from_ops(d, n, ops)
+    src = qf.qf_program_jit_source(p, dtype, adjoint=True)
+    units = [u for u in src.split("// ---- translation unit\n") if u.strip()]
+    assert units and "A.rows[" in src and "ltile" in src
+    for u in sorted(units, key=len)[-2:]:
+        rc, log = _compile(L, u)
+        assert rc == 0, log[:2000]
+    qf.qf_program_free(p)
