@@ -101,3 +101,46 @@ def test_parameters_change_without_recompiling(orc):
         assert np.abs(download(st) - orc.run(ops, d, n, params=th)).max() <= 1e-12
     qf.qf_program_free(p)
     st.free()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("d,n", [(2, 10), (3, 7), (4, 5), (5, 4), (7, 3)])
+def test_compiled_adjoint_matches_generic_and_oracle(orc, d, n, dtype):
+    """Gradient of a circuit with every parametrised kind (level-pair and
+    Gell-Mann rotations, controlled rotations with the control inside and
+    outside a register stage, a parameter shared by several gates) between
+    SWAP, custom two-qudit and multi-controlled gates: compiled reverse passes
+    against the generic sweep and the oracle's derivative circuits."""
+    qf = gpu_lib()
+    rng = np.random.default_rng(d * 10 + n)
+    ops = [W.Op("h", (q,)) for q in range(n)]
+    slot = 0
+    for q in range(n):
+        ops.append(W.Op("rot", (q,), j=0, k=d - 1, axis="x", param=slot)); slot += 1
+        ops.append(W.Op("rot", (q,), j=d - 1, axis="g", param=slot)); slot += 1
+    ops += [W.Op("crot", (0, n - 1), j=0, k=1, axis="y", param=slot),
+            W.Op("crot", (n - 1, 0), j=0, k=d - 1, axis="z", param=slot + 1),
+            W.Op("swap", (0, n - 1)), W.Op("mcx", (0, 1, n - 1)),
+            W.Op("crot", (1, n - 1), j=d - 1, axis="g", param=slot + 2),
+            W.Op("rot", (n - 1,), j=0, k=1, axis="y", param=0)]
+    if d * d <= 64:
+        ops.append(W.Op("u", (1, 0), matrix=W.haar_unitary(d * d, rng)))
+    ops.append(W.Op("crot", (n - 1, 1), j=0, k=1, axis="x", param=slot + 3))
+    P = slot + 4
+    theta = W.normal_angles(P, seed=P + d)
+    w = np.linspace(0.5, 1.5, n)
+    want = orc.grad_bruteforce(ops, d, n, theta, w)
+    p = qf.program_from_ops(d, n, ops)
+    psi, lam = qf.State(d, n, dtype), qf.State(d, n, dtype)
+    grads = []
+    for jit in (True, False):
+        qf.qf_program_set_jit(p, jit)
+        psi.set_basis(0)
+        _, g = qf.qf_program_gradient(p, psi.handle, lam.handle, theta, w)
+        grads.append(g)
+    at = 1e-10 if dtype == "c128" else 1e-4 * max(1.0, np.abs(want).max())
+    assert np.abs(grads[0] - want).max() <= at
+    assert np.abs(grads[1] - want).max() <= at
+    qf.qf_program_free(p)
+    psi.free()
+    lam.free()
