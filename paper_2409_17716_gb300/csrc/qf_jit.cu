@@ -154,6 +154,13 @@ __device__ __forceinline__ void qj_cp(C *dst, const C *src) {
                  : "memory");
 }
 __device__ __forceinline__ void qj_wait() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory"); }
+// two complex64 amplitudes (16 bytes, both addresses 16-byte aligned)
+__device__ __forceinline__ void qj_cp2(C *dst, const C *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(qj_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void qj_st2(C *dst, const C *src) {
+    *reinterpret_cast<float4 *>(dst) = *reinterpret_cast<const float4 *>(src);
+}
 )";
 
 constexpr int kParamPoolMax = 1800;   // pool entries passed as kernel parameters (16 bytes each)
@@ -202,18 +209,14 @@ class Gen {
         o_ << "  __syncthreads();\n";
         o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
         o_ << "    const long long base = qj_base;\n";
-        o_ << "    const C *src = A.psi + base;\n";
-        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
-           << "; qj_cp(tile + e, src + offA[a] + (e - a * " << p_.SEG << ")); }\n";
+        transfer(true, {{"tile", "A.psi"}});
         o_ << "    qj_wait();\n    __syncthreads();\n";
         for (const TStage &st : p_.stages) {
             if (st.legacy) legacy(p_.ops[st.first]);
             else stage(st);
             o_ << "    __syncthreads();\n";
         }
-        o_ << "    C *dst = A.psi + base;\n";
-        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
-           << "; dst[offA[a] + (e - a * " << p_.SEG << ")] = tile[e]; }\n";
+        transfer(false, {{"tile", "A.psi"}});
         o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
            << "(A, t + gridDim.x);\n";
         o_ << "    __syncthreads();\n  }\n}\n";
@@ -249,9 +252,7 @@ class Gen {
         o_ << "  __syncthreads();\n";
         o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
         o_ << "    const long long base = qj_base;\n";
-        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
-           << "; const long long gi = base + offA[a] + (e - a * " << p_.SEG
-           << "); qj_cp(tile + e, A.psi + gi); qj_cp(ltile + e, A.lam + gi); }\n";
+        transfer(true, {{"tile", "A.psi"}, {"ltile", "A.lam"}});
         o_ << "    qj_wait();\n    __syncthreads();\n";
         for (const TStage &st : p_.stages) {
             if (st.legacy) {
@@ -265,9 +266,7 @@ class Gen {
             }
             o_ << "    __syncthreads();\n";
         }
-        o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") { const int a = e / " << p_.SEG
-           << "; const long long gi = base + offA[a] + (e - a * " << p_.SEG
-           << "); A.psi[gi] = tile[e]; A.lam[gi] = ltile[e]; }\n";
+        transfer(false, {{"tile", "A.psi"}, {"ltile", "A.lam"}});
         o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
            << "(A, t + gridDim.x);\n";
         o_ << "    __syncthreads();\n  }\n";
@@ -282,6 +281,32 @@ class Gen {
                << " + c] = 2.0 * s; }\n";
         }
         o_ << "}\n";
+    }
+
+    // Tile load (cp.async) or store between shared memory and the d^kA runs
+    // of SEG amplitudes at base + offA[a].  Complex64 at even d moves
+    // amplitude pairs (every run start is even, so 16-byte aligned); runs of
+    // at least 64 transfers are walked run by run without index division.
+    void transfer(bool load, const std::vector<std::pair<std::string, std::string>> &bufs) {
+        const int pf = (!p_.c128 && D_ % 2 == 0 && p_.SEG % 2 == 0) ? 2 : 1;
+        const int per_run = p_.SEG / pf, NA = p_.T / p_.SEG;
+        auto one = [&](const std::string &sm, const std::string &g, const std::string &e, const std::string &gi) {
+            if (load) o_ << (pf == 2 ? "qj_cp2(" : "qj_cp(") << sm << " + " << e << ", " << g << " + " << gi << "); ";
+            else if (pf == 2) o_ << "qj_st2(" << g << " + " << gi << ", " << sm << " + " << e << "); ";
+            else o_ << g << "[" << gi << "] = " << sm << "[" << e << "]; ";
+        };
+        if (per_run >= 64) {
+            o_ << "    for (int a = 0; a < " << NA << "; ++a) { const long long ro = base + offA[a];\n";
+            o_ << "      for (int l = tid * " << pf << "; l < " << p_.SEG << "; l += " << p_.threads * pf << ") { ";
+            for (auto &b : bufs) one(b.first, b.second, "a * " + std::to_string(p_.SEG) + " + l", "ro + l");
+            o_ << "}\n    }\n";
+        } else {
+            o_ << "    for (int e = tid * " << pf << "; e < " << p_.T << "; e += " << p_.threads * pf
+               << ") { const int a = e / " << p_.SEG << "; const long long gi = base + offA[a] + (e - a * " << p_.SEG
+               << "); ";
+            for (auto &b : bufs) one(b.first, b.second, "e", "gi");
+            o_ << "}\n";
+        }
     }
 
     void tile_base_fn(const std::string &name) {
