@@ -303,10 +303,11 @@ __device__ __forceinline__ double adj_block_sum(double v, double *red) {
     return s;
 }
 
-// Im(conj(a) * b)
+// Im(conj(a) * b), in the precision of the amplitudes (FP64 is far slower
+// than FP32 on this GPU; each thread's sum is widened at the block reduction)
 template <typename C>
-__device__ __forceinline__ double im_conj_mul(C a, C b) {
-    return (double)a.x * (double)b.y - (double)a.y * (double)b.x;
+__device__ __forceinline__ auto im_conj_mul(C a, C b) -> decltype(a.x) {
+    return a.x * b.y - a.y * b.x;
 }
 
 template <typename R, int D>
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
     const TOp &op = A.op;
     const long long S = A.S;
     C *psi = A.psi, *lam = A.lam;
-    double g = 0.0;
+    R g = 0;
     // grid-stride over fibres: the grid is capped so each gate leaves a few
     // hundred gradient rows, not one per 256 fibres
     for (uint32_t f = blockIdx.x * kStridedBlock + threadIdx.x; f < A.nfib; f += gridDim.x * kStridedBlock) {
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
             if (A.grad) {
                 const C ga = cfma(A.gen[1], b, cmul(A.gen[0], a));
                 const C gb = cfma(A.gen[3], b, cmul(A.gen[2], a));
-                g += (im_conj_mul(la, ga) + im_conj_mul(lb, gb)) * (ctrl ? (double)ctl : 1.0);
+                g += (im_conj_mul(la, ga) + im_conj_mul(lb, gb)) * (ctrl ? (R)ctl : (R)1);
             }
             const C *M = A.m + (ctrl ? 4 * ctl : 0);
             psi[idx + op.j * S] = cfma(M[1], b, cmul(M[0], a));
@@ -367,16 +368,16 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
             const bool ctrl = op.kind == OP_CDIAG;
             if (ctrl && ctl == 0) break;
             const C *M = A.m + (ctrl ? d * ctl : 0);
-            double t = 0.0;
+            R t = 0;
 #pragma unroll
             for (int l = 0; l < DM; ++l)
                 if (l < d && ((op.mask >> l) & 1)) {
                     const C v = psi[idx + l * S], w = lam[idx + l * S];
-                    if (A.grad) t += (double)A.gen[l].x * im_conj_mul(w, v);
+                    if (A.grad) t += A.gen[l].x * im_conj_mul(w, v);
                     psi[idx + l * S] = cmul(M[l], v);
                     lam[idx + l * S] = cmul(M[l], w);
                 }
-            g += t * (ctrl ? (double)ctl : 1.0);
+            g += t * (ctrl ? (R)ctl : (R)1);
             break;
         }
         case OP_SHIFT:
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(kStridedBlock) k_strided_adj(const __grid_cons
         }
     }
     if (A.grad) {
-        const double s = adj_block_sum(g, red);
+        const double s = adj_block_sum((double)g, red);
         if (threadIdx.x == 0) A.rows[blockIdx.x] = 2.0 * s;
     }
 }
