@@ -154,6 +154,9 @@ __device__ __forceinline__ void qj_cp(C *dst, const C *src) {
                  : "memory");
 }
 __device__ __forceinline__ void qj_wait() { asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void qj_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void qj_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void qj_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 // two complex64 amplitudes (16 bytes, both addresses 16-byte aligned)
 __device__ __forceinline__ void qj_cp2(C *dst, const C *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(qj_smem(dst)), "l"(src) : "memory");
@@ -178,6 +181,8 @@ struct PassSrc {
     bool c128, params;   // params: entries in the kernel parameters, else global
     int npool;
     bool adj = false;    // reverse pass of the adjoint sweep (psi and lambda, gradient columns)
+    long long ntiles = 0;                        // tiles of the pass
+    std::vector<long long> runM, runS, strideA;  // tile geometry (literals in the source)
     int ncols = 0;       // gradient columns (parametrised ops, op.gcol) of an adjoint pass
     std::vector<TOp> ops;
     std::vector<TStage> stages;
@@ -187,39 +192,73 @@ class Gen {
   public:
     Gen(const PassSrc &p, std::ostringstream &o) : p_(p), o_(o), D_(p.d) {}
 
+    // Forward pass.  With A.mode != 0 tiles are double-buffered: while a CTA
+    // applies the gates to one tile, the copy of its next tile is in flight,
+    // so the barrier after a tile's load rarely waits on HBM; the host picks
+    // that mode only where the second buffer costs no CTAs per SM.  The tile
+    // geometry is literal (tile bases by division by constants in every
+    // thread).  Shared memory: run offsets, then one or two tiles.
     void kernel(const std::string &name) {
         const int NG = std::max(1, 2 * p_.nruns + p_.kA);
         const int NP = std::max(1, p_.params ? p_.npool : 1);
         const int NA = p_.T / p_.SEG;
-        o_ << "struct __align__(16) A_" << name << " { C *psi; const P *gp; long long ntiles; long long geo[" << NG
+        const size_t boff = ((size_t)NA * 8 + 15) & ~(size_t)15;
+        o_ << "struct __align__(16) A_" << name << " { C *psi; const P *gp; long long mode; long long geo[" << NG
            << "]; P pool[" << NP << "]; };\n";
         o_ << "extern \"C\" __global__ void __launch_bounds__(" << p_.threads << ") " << name
            << "(const __grid_constant__ A_" << name << " A) {\n";
         o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
-        o_ << "  __shared__ long long qj_base;\n";
-        o_ << "  C *tile = reinterpret_cast<C *>(qj_sm);\n";
-        o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm + " << (size_t)p_.T * elt() << ");\n";
+        o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm);\n";
+        o_ << "  C *buf0 = reinterpret_cast<C *>(qj_sm + " << boff << ");\n";
+        o_ << "  C *buf1 = buf0 + " << p_.T << ";\n";
         o_ << "  const int tid = threadIdx.x;\n";
-        // run offsets of the active qudits
-        o_ << "  for (int a = tid; a < " << NA << "; a += " << p_.threads << ") {\n    long long o = 0; int rem = a;\n";
-        for (int i = p_.kA - 1; i >= 0; --i)
-            o_ << "    o += (long long)(rem % " << D_ << ") * A.geo[" << 2 * p_.nruns + i << "]; rem /= " << D_ << ";\n";
-        o_ << "    offA[a] = o;\n  }\n";
-        o_ << "  if (tid == 0) qj_base = qj_tile_base_" << name << "(A, blockIdx.x);\n";
+        o_ << "  const bool db = A.mode != 0;\n";
+        emit_offA(NA);
         o_ << "  __syncthreads();\n";
-        o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
-        o_ << "    const long long base = qj_base;\n";
+        o_ << "  long long t = blockIdx.x;\n";
+        o_ << "  if (db && t < " << p_.ntiles << ") { C *tile = buf0; const long long base = qj_tb_" << name << "(t);\n";
         transfer(true, {{"tile", "A.psi"}});
-        o_ << "    qj_wait();\n    __syncthreads();\n";
+        o_ << "    qj_commit();\n  }\n";
+        o_ << "  for (int it = 0; t < " << p_.ntiles << "; ++it, t += gridDim.x) {\n";
+        o_ << "    C *tile = (db && (it & 1)) ? buf1 : buf0;\n";
+        o_ << "    const long long base = qj_tb_" << name << "(t);\n";
+        o_ << "    if (db) {\n      const long long tn = t + gridDim.x;\n      if (tn < " << p_.ntiles
+           << ") { C *tile = (it & 1) ? buf0 : buf1; const long long base = qj_tb_" << name << "(tn);\n";
+        transfer(true, {{"tile", "A.psi"}});
+        o_ << "      }\n      qj_commit();\n      qj_wait1();\n    } else {\n";
+        transfer(true, {{"tile", "A.psi"}});
+        o_ << "      qj_commit();\n      qj_wait0();\n    }\n";
+        o_ << "    __syncthreads();\n";
         for (const TStage &st : p_.stages) {
             if (st.legacy) legacy(p_.ops[st.first]);
             else stage(st);
             o_ << "    __syncthreads();\n";
         }
         transfer(false, {{"tile", "A.psi"}});
-        o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
-           << "(A, t + gridDim.x);\n";
-        o_ << "    __syncthreads();\n  }\n}\n";
+        o_ << "    __syncthreads();\n  }\n  qj_wait0();\n}\n";
+    }
+
+    // offA[a] = offset of run a: digits of a on the active qudits (literal strides).
+    void emit_offA(int NA) {
+        o_ << "  for (int a = tid; a < " << NA << "; a += " << p_.threads << ") {\n    long long o = 0; int rem = a;\n";
+        for (int i = p_.kA - 1; i >= 0; --i)
+            o_ << "    o += (long long)(rem % " << D_ << ") * " << p_.strideA[i] << "LL; rem /= " << D_ << ";\n";
+        o_ << "    offA[a] = o;\n  }\n";
+    }
+
+    // Base offset of tile t: the outer qudits' digits, runs from the least
+    // significant (literal radices and strides).
+    void tile_base_lit(const std::string &name) {
+        const bool narrow = p_.ntiles < (1ll << 32);
+        o_ << "__device__ __forceinline__ long long qj_tb_" << name << "(long long tl) {\n  long long base = 0;\n";
+        if (narrow) o_ << "  unsigned t = (unsigned)tl;\n";
+        else o_ << "  unsigned long long t = (unsigned long long)tl;\n";
+        for (int r = 0; r < p_.nruns; ++r) {
+            const std::string M = std::to_string(p_.runM[r]) + (narrow ? "u" : "ull");
+            o_ << "  { const auto q = t / " << M << "; base += (long long)(t - q * " << M << ") * " << p_.runS[r]
+               << "LL; t = q; }\n";
+        }
+        o_ << "  return base;\n}\n";
     }
 
     // Reverse pass of the adjoint sweep: psi and lambda tiles; every op is
@@ -653,6 +692,9 @@ int jit_stage_k(int d, bool c128) {
 }
 
 struct JitPassInfo {
+    size_t smem2 = 0;       // forward passes: shared memory with a double buffer (0: not offered)
+    bool dbuf = false;      // forward passes: double-buffered tiles chosen
+    bool l1_copies = false; // tile copies of 8 bytes through L1 (complex64 at odd d or odd runs)
     int ncols = 0;          // gradient columns (adjoint passes)
     size_t header = 24;     // bytes of pointers and tile count before geo[]
     CUfunction fn = nullptr;
@@ -691,6 +733,10 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.nt = pp.geom.nt;
         ps.kA = pp.geom.kA;
         ps.nruns = pp.geom.nruns;
+        ps.ntiles = pp.geom.ntiles;
+        ps.runM.assign(pp.geom.runM, pp.geom.runM + pp.geom.nruns);
+        ps.runS.assign(pp.geom.runS, pp.geom.runS + pp.geom.nruns);
+        ps.strideA.assign(pp.geom.strideA, pp.geom.strideA + pp.geom.kA);
         ps.adj = adj;
         ps.K = std::min(k_override > 0 ? k_override : (adj ? jit_stage_k_adj(d, c128) : jit_stage_k(d, c128)), pp.geom.nt);
         ps.ops = ops[pi];
@@ -729,12 +775,20 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n" << kPrelude;
         Gen g(ps, src);
         g.tile_base_fn(names[pi]);
+        g.tile_base_lit(names[pi]);
         if (adj) g.kernel_adj(names[pi]);
         else g.kernel(names[pi]);
         out[pi] = src.str();
         JitPassInfo &ji = jp->passes[pi];
         ji.threads = ps.threads;
-        ji.smem = (size_t)(adj ? 2 : 1) * ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;
+        if (adj) {
+            ji.smem = (size_t)2 * ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;   // psi and lambda tiles
+        } else {
+            const size_t boff = ((size_t)(ps.T / ps.SEG) * 8 + 15) & ~(size_t)15;
+            ji.smem = boff + (size_t)ps.T * (c128 ? 16 : 8);         // single buffer
+            ji.smem2 = boff + (size_t)2 * ps.T * (c128 ? 16 : 8);    // double buffer
+            ji.l1_copies = !c128 && !(d % 2 == 0 && ps.SEG % 2 == 0);
+        }
         ji.ncols = ps.ncols;
         ji.header = adj ? 40 : 24;
         ji.params = ps.params;
@@ -891,10 +945,22 @@ qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<T
         }
         JitPassInfo &ji = jp->passes[pi];
         CUresult r = g_drv.get_function(&ji.fn, mod, names[pi].c_str());
-        if (r == CUDA_SUCCESS && ji.smem > 48 * 1024)
-            r = g_drv.set_attribute(ji.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ji.smem);
+        const size_t smax = std::max(ji.smem, ji.smem2);
+        if (r == CUDA_SUCCESS && smax > 48 * 1024)
+            r = g_drv.set_attribute(ji.fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smax);
         int per_sm = 0;
         if (r == CUDA_SUCCESS) r = g_drv.occupancy(&per_sm, ji.fn, ji.threads, ji.smem);
+        if (r == CUDA_SUCCESS && ji.smem2 > 0 && per_sm > 0) {
+            // double-buffer only where the second tile costs no CTAs per SM
+            // and, for passes whose 8-byte copies go through L1, leaves the
+            // SM at least ~67 KB of it
+            int per_sm2 = 0;
+            r = g_drv.occupancy(&per_sm2, ji.fn, ji.threads, ji.smem2);
+            if (r == CUDA_SUCCESS && per_sm2 >= per_sm && (!ji.l1_copies || (size_t)per_sm * ji.smem2 <= 160 * 1024)) {
+                ji.dbuf = true;
+                ji.smem = ji.smem2;
+            }
+        }
         if (r != CUDA_SUCCESS || per_sm < 1) {
             delete jp;
             return set_error(QF_ERR_CUDA, "tile pass kernel setup failed: " + cuda_err(r));
@@ -924,7 +990,8 @@ qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void 
     std::vector<unsigned char> args(ji.arg_bytes, 0);
     std::memcpy(args.data(), &psi, 8);
     std::memcpy(args.data() + 8, &gpool, 8);
-    std::memcpy(args.data() + 16, &g.ntiles, 8);
+    const long long mode = ji.dbuf ? 1 : 0;
+    std::memcpy(args.data() + 16, &mode, 8);
     long long geo[2 * (kMaxActive + 1) + kMaxActive] = {};
     for (int r = 0; r < g.nruns; ++r) {
         geo[r] = g.runM[r];
