@@ -276,7 +276,6 @@ class Gen {
         o_ << "extern \"C\" __global__ void __launch_bounds__(" << p_.threads << ") " << name
            << "(const __grid_constant__ A_" << name << " A) {\n";
         o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
-        o_ << "  __shared__ long long qj_base;\n";
         o_ << "  __shared__ double qj_red[" << std::max(1, NC * WARPS) << "];\n";
         o_ << "  C *tile = reinterpret_cast<C *>(qj_sm);\n";
         o_ << "  C *ltile = tile + " << p_.T << ";\n";
@@ -287,10 +286,9 @@ class Gen {
         for (int i = p_.kA - 1; i >= 0; --i)
             o_ << "    o += (long long)(rem % " << D_ << ") * A.geo[" << 2 * p_.nruns + i << "]; rem /= " << D_ << ";\n";
         o_ << "    offA[a] = o;\n  }\n";
-        o_ << "  if (tid == 0) qj_base = qj_tile_base_" << name << "(A, blockIdx.x);\n";
         o_ << "  __syncthreads();\n";
-        o_ << "  for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {\n";
-        o_ << "    const long long base = qj_base;\n";
+        o_ << "  for (long long t = blockIdx.x; t < " << p_.ntiles << "; t += gridDim.x) {\n";
+        o_ << "    const long long base = qj_tb_" << name << "(t);\n";
         transfer(true, {{"tile", "A.psi"}, {"ltile", "A.lam"}});
         o_ << "    qj_wait();\n    __syncthreads();\n";
         for (const TStage &st : p_.stages) {
@@ -306,8 +304,6 @@ class Gen {
             o_ << "    __syncthreads();\n";
         }
         transfer(false, {{"tile", "A.psi"}, {"ltile", "A.lam"}});
-        o_ << "    if (tid == 0 && t + gridDim.x < A.ntiles) qj_base = qj_tile_base_" << name
-           << "(A, t + gridDim.x);\n";
         o_ << "    __syncthreads();\n  }\n";
         if (NC > 0) {
             o_ << "  const int lane = tid & 31, wid = tid >> 5;\n";
@@ -348,15 +344,6 @@ class Gen {
         }
     }
 
-    void tile_base_fn(const std::string &name) {
-        o_ << "struct A_" << name << ";\n";
-        o_ << "template <typename AT> __device__ __forceinline__ long long qj_tile_base_" << name
-           << "(const AT &A, long long t) {\n  long long base = 0;\n";
-        for (int r = 0; r < p_.nruns; ++r)
-            o_ << "  { const long long q = t / A.geo[" << r << "]; base += (t - q * A.geo[" << r << "]) * A.geo["
-               << p_.nruns + r << "]; t = q; }\n";
-        o_ << "  return base;\n}\n";
-    }
 
     size_t elt() const { return p_.c128 ? 16 : 8; }
 
@@ -774,7 +761,6 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         std::ostringstream src;
         src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n" << kPrelude;
         Gen g(ps, src);
-        g.tile_base_fn(names[pi]);
         g.tile_base_lit(names[pi]);
         if (adj) g.kernel_adj(names[pi]);
         else g.kernel(names[pi]);
