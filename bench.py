@@ -697,15 +697,21 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
     for _ in range(2):
         step()
     torch.cuda.synchronize()
-    # plain host-to-device bandwidth of the pinned buffers, for context
+    # plain host-to-device bandwidth of the pinned buffers on the copy
+    # stream, for context (best of three)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for st, h in zip(states, host):
-        st.tensor.copy_(h, non_blocking=True)
-    e1.record()
-    torch.cuda.synchronize()
-    h2d_gbs = sum(h.numel() * 8 for h in host) / (e0.elapsed_time(e1) / 1e3) / 1e9
+    best_ms = None
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record(copy_s)
+        with torch.cuda.stream(copy_s):
+            for st, h in zip(states, host):
+                st.tensor.copy_(h, non_blocking=True)
+        e1.record(copy_s)
+        torch.cuda.synchronize()
+        ms_c = e0.elapsed_time(e1)
+        best_ms = ms_c if best_ms is None else min(best_ms, ms_c)
+    h2d_gbs = sum(h.numel() * 8 for h in host) / (best_ms / 1e3) / 1e9
     steps = max(3, args.steps // 4)
     t0 = time.perf_counter()
     for _ in range(steps):
