@@ -306,7 +306,7 @@ cudaError_t batch_prepare(int d, bool adj, size_t smem, int *per_sm) {
 #define QF_CASE(DD)                                                                              \
     case DD:                                                                                     \
         return adj ? batch_prepare_d<R, DD, true>(smem, per_sm) : batch_prepare_d<R, DD, false>(smem, per_sm);
-        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
+        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8) QF_CASE(10)
 #undef QF_CASE
     default:
         return adj ? batch_prepare_d<R, 0, true>(smem, per_sm) : batch_prepare_d<R, 0, false>(smem, per_sm);
@@ -340,7 +340,7 @@ cudaError_t launch_batch(cudaStream_t stream, int d, bool adj, int grid, size_t 
         if (adj) k_batch<R, DD, true><<<grid, kTileBlock, smem, stream>>>(A, d);               \
         else k_batch<R, DD, false><<<grid, kTileBlock, smem, stream>>>(A, d);                  \
         break;
-        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8)
+        QF_CASE(2) QF_CASE(3) QF_CASE(4) QF_CASE(5) QF_CASE(6) QF_CASE(7) QF_CASE(8) QF_CASE(10)
 #undef QF_CASE
     default:
         if (adj) k_batch<R, 0, true><<<grid, kTileBlock, smem, stream>>>(A, d);
