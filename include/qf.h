@@ -276,7 +276,7 @@ qf_status qf_program_add_mcu(qf_program *p, const int *controls, const int *leve
  * compiler log) if a pass fails to compile. */
 qf_status qf_program_set_jit(qf_program *p, int enable);
 /* Qudits held in registers per stage of a compiled tile pass (1..6; 0 = the
- * default for d, 4 for d = 2 and 2 for d = 3..5 in complex64): more slots
+ * default for d, 5 for d = 2 and 2 for d = 3..5 in complex64): more slots
  * mean fewer shared-memory round trips and more registers per thread. */
 qf_status qf_program_set_stage_slots(qf_program *p, int slots);
 /* The CUDA source the program's tile passes compile from (for dtype dt; the
@@ -288,12 +288,15 @@ qf_status qf_program_set_fusion(qf_program *p, int enable);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
  * per shared-memory tile (default: the largest t with d^t amplitudes <= 8192
- * for complex64 / 4096 for complex128; a forward-pass override may go up to
- * 160 KiB of amplitudes per tile); min_run_qudits = lowest qudits always in
- * the tile, so every contiguous run read from HBM has d^r amplitudes (default
- * 5, 3, 2, 1 for d = 2, 3, 4, 5, chosen by measurement; otherwise the smallest
- * r with d^r >= 32); max_ops = gates per pass (<= 96).  Takes
- * effect at the next run. */
+ * for complex64 / 4096 for complex128, and 12 for forward passes of qubits in
+ * complex64; a forward-pass override may go up to 160 KiB of amplitudes per
+ * tile, single-buffered where two tiles exceed a CTA's shared memory);
+ * min_run_qudits = lowest qudits always in the tile, so every contiguous run
+ * read from HBM has d^r amplitudes (default 5, 3, 2, 1 for d = 2, 3, 4, 5 and
+ * 4 for forward passes of qubits in complex64, chosen by measurement;
+ * otherwise the smallest r with d^r >= 32); max_ops = gates per pass (<= 96).
+ * Takes effect at the next run.  QF_ERR_ARG at run time if a pass would need
+ * more shared memory than a CTA may hold. */
 qf_status qf_program_set_tiling(qf_program *p, int tile_qudits, int min_run_qudits, int max_ops);
 
 /* Applies the program to s (same d and n).  params: host FP64 vector of

@@ -675,7 +675,7 @@ int jit_stage_k_adj(int d, bool c128) {
 
 int jit_stage_k(int d, bool c128) {
     if (c128) return d == 2 ? 3 : (d == 3 || d == 4) ? 2 : 1;
-    return d == 2 ? 4 : d <= 5 ? 2 : 1;
+    return d == 2 ? 5 : d <= 5 ? 2 : 1;
 }
 
 struct JitPassInfo {
@@ -887,6 +887,8 @@ qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<T
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     const std::string arch = "--gpu-architecture=sm_" + std::to_string(major) + std::to_string(minor) + "a";
+    int smem_optin = 0;   // largest dynamic shared memory a CTA may opt in to
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const std::string dir = cache_dir();
     if (!dir.empty()) mkdir(dir.c_str(), 0755);
     const size_t np = plan.size();
@@ -930,6 +932,13 @@ qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<T
             if (need[pi] && !dir.empty()) write_file(dir + "/" + keys[pi] + ".cubin", cubins[pi]);
         }
         JitPassInfo &ji = jp->passes[pi];
+        if (ji.smem > (size_t)smem_optin) {
+            delete jp;
+            return set_error(QF_ERR_ARG, "a tile pass needs " + std::to_string(ji.smem) +
+                                             " bytes of shared memory, above the " + std::to_string(smem_optin) +
+                                             " a CTA may hold");
+        }
+        if (ji.smem2 > (size_t)smem_optin) ji.smem2 = 0;   // a second tile does not fit: single buffer
         CUresult r = g_drv.get_function(&ji.fn, mod, names[pi].c_str());
         const size_t smax = std::max(ji.smem, ji.smem2);
         if (r == CUDA_SUCCESS && smax > 48 * 1024)

@@ -3,7 +3,7 @@ interpreting tile kernel and the oracle: every gate kind in fused passes
 (SWAP and custom two-qudit gates through shared memory, controls inside and
 outside a register stage, multi-controlled passes in between), complex64 and
 complex128, every d with a compiled stage layout (2-5) and one above it (7),
-overridden stage slots, and a pass whose gate entries exceed the
+overridden stage slots and tilings, and a pass whose gate entries exceed the
 kernel-parameter budget (read from device memory instead)."""
 import numpy as np
 import pytest
@@ -56,6 +56,28 @@ def test_stage_slot_overrides(orc, slots):
     st = qf.State(d, n, "c64").set_basis(0)
     qf.qf_program_run(p, st.handle)
     assert np.abs(download(st) - orc.run(ops, d, n)).max() <= tol("c64", len(ops))
+    qf.qf_program_free(p)
+    st.free()
+
+
+@pytest.mark.parametrize("d,n,dtype,tile,run", [
+    (2, 16, "c64", 14, 0), (2, 16, "c64", 12, 4), (2, 15, "c128", 13, 0), (3, 11, "c64", 9, 0),
+    (3, 10, "c128", 8, 2), (4, 9, "c64", 7, 1), (5, 8, "c64", 6, 2)])
+def test_tiling_overrides(orc, d, n, dtype, tile, run):
+    """Tile and run overrides up to the largest tile (160 KiB of amplitudes,
+    where a second buffer no longer fits in a CTA's shared memory), compiled
+    and generic."""
+    qf = gpu_lib()
+    ops = all_kinds(d, n, np.random.default_rng(d + 40))
+    want = orc.run(ops, d, n)
+    p = qf.program_from_ops(d, n, ops)
+    qf.qf_program_set_tiling(p, tile, run, 0)
+    st = qf.State(d, n, dtype)
+    for jit in (True, False):
+        qf.qf_program_set_jit(p, jit)
+        st.set_basis(0)
+        qf.qf_program_run(p, st.handle)
+        assert np.abs(download(st) - want).max() <= tol(dtype, len(ops)), (jit, tile, run)
     qf.qf_program_free(p)
     st.free()
 
