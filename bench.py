@@ -679,12 +679,17 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
     for ev in done:
         ev.record(comp_s)
 
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
     def step():
         for i, (st, h) in enumerate(zip(states, host)):
             copy_s.wait_event(done[i])          # the previous step is done with this state
+            if i == 0:
+                c0.record(copy_s)
             with torch.cuda.stream(copy_s):
                 st.tensor.copy_(h, non_blocking=True)
             copied[i].record(copy_s)
+        c1.record(copy_s)
         for i, (st, p) in enumerate(zip(states, progs)):
             comp_s.wait_event(copied[i])
             with torch.cuda.stream(comp_s):
@@ -712,10 +717,15 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
         ms_c = e0.elapsed_time(e1)
         best_ms = ms_c if best_ms is None else min(best_ms, ms_c)
     h2d_gbs = sum(h.numel() * 8 for h in host) / (best_ms / 1e3) / 1e9
-    steps = max(3, args.steps // 4)
+    steps = max(3, args.steps // 2)
+    per_step, copy_ms = [], []
     t0 = time.perf_counter()
     for _ in range(steps):
+        ts = time.perf_counter()
         step()
+        per_step.append(1e3 * (time.perf_counter() - ts))
+        c1.synchronize()
+        copy_ms.append(c0.elapsed_time(c1))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     for st in states:
@@ -724,6 +734,8 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
     return {"value": au / dt, "unit": UNIT, "h2d_bytes_per_step": sum(d ** n * 8 for d, n in sizes),
             "d2h_bytes_per_step": sum((n + 1) * 8 for d, n in sizes), "steps": steps,
             "h2d_gbs_measured": h2d_gbs,
+            "step_ms": {"min": min(per_step), "median": sorted(per_step)[len(per_step) // 2], "max": max(per_step)},
+            "copy_ms_median": sorted(copy_ms)[len(copy_ms) // 2],
             "note": "per state: pinned-host copy in (copy stream), fused program and <N_q> back (compute stream, "
                     "starts when the state's copy lands)"}
 

@@ -754,7 +754,12 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.npool = npool;
         ps.params = npool <= kParamPoolMax && !dense_k;
         const int DK = ipow_i(d, ps.K);
-        ps.threads = (ps.T / DK <= 128) ? 128 : 256;
+        // one register block per thread and stage where 128 threads cover
+        // them; forward complex64 passes with up to 256 blocks also run 128
+        // threads (two blocks each: 3 % faster at d=4 on GB300, more CTAs
+        // per SM)
+        const int nblk = ps.T / DK;
+        ps.threads = (nblk <= 128 || (!adj && !c128 && nblk <= 256)) ? 128 : 256;
         std::ostringstream nm;
         nm << (adj ? "k_tile_adj_jit_d" : "k_tile_jit_d") << d << (c128 ? "_c128_" : "_c64_") << pi;
         names[pi] = nm.str();
