@@ -736,6 +736,8 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
             "h2d_gbs_measured": h2d_gbs,
             "step_ms": {"min": min(per_step), "median": sorted(per_step)[len(per_step) // 2], "max": max(per_step)},
             "copy_ms_median": sorted(copy_ms)[len(copy_ms) // 2],
+            "step_ms_each": [round(x, 2) for x in per_step],
+            "value_at_median_step": au / steps / (sorted(per_step)[len(per_step) // 2] / 1e3),
             "note": "per state: pinned-host copy in (copy stream), fused program and <N_q> back (compute stream, "
                     "starts when the state's copy lands)"}
 
