@@ -99,3 +99,40 @@ def test_generated_adjoint_passes_compile(d, n, dtype):
         rc, log = _compile(L, u)
         assert rc == 0, log[:2000]
     qf.qf_program_free(p)
+
+
+def _tile_sizes(src):
+    import re
+    return sorted({int(x) for x in re.findall(r"buf1 = buf0 \+ (\d+);", src)} |
+                  {int(x) for x in re.findall(r"ltile = tile \+ (\d+);", src)})
+
+
+def test_tiling_defaults_and_overrides():
+    """Planner tiles as the generated source shows them: forward qubit passes
+    in complex64 on 4096-amplitude tiles (the adjoint keeps 8192, complex128
+    4096), d=4 forward passes on 128-thread CTAs, and tile overrides up to the
+    160 KiB limit (larger requests clamp to it)."""
+    ops2 = W.random_circuit(2, 16, 60)
+    p = qf.program_from_ops(2, 16, ops2)
+    assert _tile_sizes(qf.qf_program_jit_source(p, qf.QF_C64)) == [4096]
+    assert _tile_sizes(qf.qf_program_jit_source(p, qf.QF_C64, adjoint=True)) == [8192]
+    assert _tile_sizes(qf.qf_program_jit_source(p, qf.QF_C128)) == [4096]
+    qf.qf_program_set_tiling(p, 15, 0, 0)   # 256 KiB asked: clamps to 2^14 amplitudes (128 KiB)
+    assert _tile_sizes(qf.qf_program_jit_source(p, qf.QF_C64)) == [16384]
+    qf.qf_program_free(p)
+    p = qf.program_from_ops(4, 8, W.random_circuit(4, 8, 40))
+    src = qf.qf_program_jit_source(p, qf.QF_C64)
+    assert _tile_sizes(src) == [4096] and "__launch_bounds__(128)" in src and "__launch_bounds__(256)" not in src
+    qf.qf_program_free(p)
+
+
+@pytest.mark.parametrize("d,n,tile,run", [(3, 11, 9, 0), (5, 8, 6, 2), (2, 16, 14, 4)])
+def test_large_tile_passes_compile(d, n, tile, run):
+    L = _nvrtc()
+    p = qf.program_from_ops(d, n, W.random_circuit(d, n, 60))
+    qf.qf_program_set_tiling(p, tile, run, 0)
+    units = _units(p, qf.QF_C64)
+    assert _tile_sizes("".join(units)) == [d ** tile]
+    rc, log = _compile(L, max(units, key=len))
+    assert rc == 0, log[:2000]
+    qf.qf_program_free(p)
