@@ -48,9 +48,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip c128/unfused/sweep/e2e/cpu legs")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="small run for ncu captures: d=3 n=17 complex64 only, no extras")
-    return ap.parse_args()
+    ap.add_argument("--profile-case", nargs="?", const="3,17", default=None, metavar="D,N",
+                    help="small run for ncu captures: one state (default d=3 n=17) complex64 only, no extras")
+    args = ap.parse_args()
+    if args.profile_case is not None:
+        d, n = (int(x) for x in args.profile_case.split(","))
+        if (d, n) not in SIZES:
+            ap.error("--profile-case takes one of the bench sizes %s" % (SIZES,))
+        args.profile_case = (d, n)
+    return args
 
 
 def dist_env():
@@ -169,7 +175,7 @@ def run_reference(args, rank, world):
 
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    sizes = SIZES if not args.profile_case else [(3, 17)]
+    sizes = SIZES if not args.profile_case else [args.profile_case]
     states, circuits, pos = [], [], []
     for d, n in sizes:
         states.append(sim.basis(d, n, 0))
@@ -256,7 +262,7 @@ def main():
         torch.cuda.synchronize()
 
     hbm_peak, peak_kind = peaks()
-    sizes = [(3, 17)] if args.profile_case else SIZES
+    sizes = [args.profile_case] if args.profile_case else SIZES
     extras = not (args.no_extras or args.profile_case)
     stream = torch.cuda.current_stream()
 
@@ -324,7 +330,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.profile_case else "profile case: d=3 n=17 only",
+            "config": {"workload": WORKLOAD if not args.profile_case else
+                       "profile case: d=%d n=%d only" % args.profile_case,
                        "global_batch": len(sizes) * world, "seq_len": None,
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (1.0-2.1 GB per state), no flush",
