@@ -103,3 +103,30 @@ def test_planner_small_state_single_tile(L):
         assert strided == 0 and passes == 1   # 729 amplitudes fit one tile
     finally:
         qf.qf_program_free(p)
+
+
+def test_program_controls_validation_on_host(L):
+    """Tiling, stage-slot and multi-controlled-gate arguments are checked on
+    the host; a rejected call records nothing."""
+    import numpy as np
+    p = qf.qf_program_create(3, 4)
+    try:
+        bad = [lambda: qf.qf_program_set_tiling(p, -1, 0, 0),
+               lambda: qf.qf_program_set_stage_slots(p, 7),
+               lambda: qf.qf_program_add_mcx(p, [1, 2], 2),         # control == target
+               lambda: qf.qf_program_add_mcx(p, [1, 1], 2),         # repeated control
+               lambda: qf.qf_program_add_mcx(p, [1, 4], 2),         # qudit out of range
+               lambda: qf.qf_program_add_mcx(p, [], 2),             # no control
+               lambda: qf.qf_program_add_mcu(p, [0], [3], 1, np.eye(3)),   # control level >= d
+               lambda: qf.qf_program_create_dims([2, 1, 3])]
+        for f in bad:
+            with pytest.raises(qf.QFError) as ei:
+                f()
+            assert ei.value.status == qf.QF_ERR_ARG
+        assert qf.qf_program_info(p) == (0, 0)
+        qf.qf_program_set_tiling(p, 6, 2, 10)
+        qf.qf_program_set_stage_slots(p, 6)
+        qf.qf_program_add_mcx(p, [0, 1], 3)
+        assert qf.qf_program_info(p) == (1, 0)
+    finally:
+        qf.qf_program_free(p)
