@@ -136,3 +136,35 @@ def test_large_tile_passes_compile(d, n, tile, run):
     rc, log = _compile(L, max(units, key=len))
     assert rc == 0, log[:2000]
     qf.qf_program_free(p)
+
+
+def _compile_v(L, src):
+    prog = ctypes.c_void_p()
+    assert L.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"t.cu", 0, None, None) == 0
+    opts = [b"--gpu-architecture=sm_103a", b"-std=c++17", b"-default-device", b"--ptxas-options=-v"]
+    rc = L.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    n = ctypes.c_size_t()
+    L.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(max(n.value, 1))
+    L.nvrtcGetProgramLog(prog, log)
+    L.nvrtcDestroyProgram(ctypes.byref(prog))
+    return rc, log.value.decode(errors="replace")
+
+
+@pytest.mark.parametrize("d,n", [(2, 28), (3, 17), (4, 14), (5, 12)])
+def test_benchmark_passes_compile_without_spills(d, n):
+    """Every compiled pass of the benchmark's random 200-gate programs
+    compiles for sm_103a with no register spills (ptxas report), at the
+    default stage slots and tiling."""
+    import re
+    from concurrent.futures import ThreadPoolExecutor
+    L = _nvrtc()
+    p = qf.program_from_ops(d, n, W.random_circuit(d, n, 200))
+    units = _units(p, qf.QF_C64)
+    qf.qf_program_free(p)
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda u: _compile_v(L, u), units))
+    for rc, log in results:
+        assert rc == 0, log[:2000]
+        spills = [int(x) for x in re.findall(r"(\d+) bytes spill stores", log)]
+        assert spills and max(spills) == 0, log[-600:]
