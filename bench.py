@@ -100,7 +100,10 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        # raw samples; QF_BENCH_CLOCKS_DIR keeps them somewhere other than the temp directory
+        import tempfile
+        self.path = os.path.join(os.environ.get("QF_BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "qf_bench_clocks_rank%d.csv" % device_index)
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
