@@ -58,3 +58,19 @@ def test_reference_arm_other_ranks_idle():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.run_reference(None, 1, 2) == 0     # returns before touching args
+
+
+def test_profile_case_argument(monkeypatch):
+    """--profile-case picks one of the benchmark sizes (default d=3 n=17) and
+    rejects any other."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--profile-case"])
+    assert bench.parse().profile_case == (3, 17)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--profile-case", "5,12"])
+    assert bench.parse().profile_case == (5, 12)
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert bench.parse().profile_case is None
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--profile-case", "3,5"])
+    with pytest.raises(SystemExit):
+        bench.parse()
