@@ -222,8 +222,10 @@ qf_status qf_expect_device(qf_state *s, const qf_obs *obs, double *out_dev);
  * needed and nothing is allocated or freed: the per-CTA partial sums live in
  * one fixed 256 KiB device array (512 rows of 64 doubles) that every device
  * loading the library holds until the process exits.  Sizes: 2 <= d <= 16,
- * 1 <= n with n + 1 <= 64; anything larger is rejected with QF_ERR_ARG and a
- * message.  The first call on each device looks up the array's device
+ * n >= 1 and d^n <= 9e15 (which keeps n + 1 within the array's 64 columns);
+ * anything larger is rejected with QF_ERR_ARG and a message.  cuda_stream
+ * must belong to the current device (QF_ERR_ARG otherwise), since the array
+ * address used is the current device's.  The first call on each device looks up the array's device
  * address with that device current; make that first call before any stream
  * capture begins.  All calls share the array and it keeps the last call's
  * contents (every value a call reads is written by that call first, so

@@ -392,16 +392,27 @@ extern "C" qf_status qf_expect_number_noalloc(const void *psi_dev, int d, int n,
     if (d < 2 || d > kMaxD) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: d must be in [2, 16]");
     if (dt != QF_C64 && dt != QF_C128) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: unknown dtype");
     if (n < 1) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: n must be >= 1");
-    if (n + 1 > kNoAllocCols)
-        return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: n = " + std::to_string(n) +
-                                         " exceeds the fixed scratch (n + 1 <= 64 outputs per CTA row)");
+    // d^n <= 9e15 is the binding limit: it implies n <= 52, so every CTA row
+    // of n + 1 outputs fits the scratch's 64 columns
     long double Nf = 1;
-    for (int i = 0; i < n; ++i) Nf *= d;
-    if (Nf > 9.0e15L) return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: d^n too large");
+    for (int i = 0; i < n && Nf <= 9.0e15L; ++i) Nf *= d;
+    if (Nf > 9.0e15L)
+        return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: d^n too large (at most 9e15 amplitudes)");
+    static_assert(kNoAllocCols >= 53, "the scratch rows must hold n + 1 outputs for every d^n <= 9e15");
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: cudaGetDevice");
+    {
+        // the scratch address looked up below belongs to the current device,
+        // so the stream must too
+        int sdev = dev;
+        e = cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev);
+        if (e != cudaSuccess) return cuda_error(e, "qf_expect_number_noalloc: cudaStreamGetDevice");
+        if (sdev != dev)
+            return set_error(QF_ERR_ARG, "qf_expect_number_noalloc: cuda_stream belongs to device " +
+                                             std::to_string(sdev) + ", not the current device " + std::to_string(dev));
+    }
     if (dev < 0 || dev >= kNoAllocMaxDevices)
         return set_error(QF_ERR_UNSUPPORTED, "qf_expect_number_noalloc: device ordinal beyond 63");
     double *partials = nullptr;

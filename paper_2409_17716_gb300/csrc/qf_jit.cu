@@ -51,6 +51,7 @@ struct Nvrtc {
     nvrtcResult (*cubin_size)(nvrtcProgram, size_t *);
     nvrtcResult (*cubin)(nvrtcProgram, char *);
     nvrtcResult (*destroy)(nvrtcProgram *);
+    nvrtcResult (*version)(int *, int *);
 };
 
 struct Driver {
@@ -67,7 +68,10 @@ bool g_loaded = false;
 std::string g_load_err;
 Nvrtc g_nv;
 Driver g_drv;
-std::map<std::string, CUmodule> g_modules;   // generated source -> loaded module
+// (device ordinal, generated source) -> loaded module: a module belongs to the
+// context it was loaded in, so each device loads its own
+std::map<std::pair<int, std::string>, CUmodule> g_modules;
+std::string g_tool_tag;   // NVRTC and driver versions: part of every cached cubin's key
 
 bool load_apis() {
     if (g_loaded) return true;
@@ -89,8 +93,9 @@ bool load_apis() {
     g_nv.cubin_size = (decltype(g_nv.cubin_size))sym("nvrtcGetCUBINSize");
     g_nv.cubin = (decltype(g_nv.cubin))sym("nvrtcGetCUBIN");
     g_nv.destroy = (decltype(g_nv.destroy))sym("nvrtcDestroyProgram");
+    g_nv.version = (decltype(g_nv.version))sym("nvrtcVersion");
     if (!g_nv.create || !g_nv.compile || !g_nv.log_size || !g_nv.log || !g_nv.cubin_size || !g_nv.cubin ||
-        !g_nv.destroy) {
+        !g_nv.destroy || !g_nv.version) {
         g_load_err = "NVRTC symbols missing";
         return false;
     }
@@ -107,6 +112,10 @@ bool load_apis() {
         g_load_err = "CUDA driver entry points for module loading are unavailable";
         return false;
     }
+    int vmaj = 0, vmin = 0, drv_ver = 0;
+    g_nv.version(&vmaj, &vmin);
+    cudaDriverGetVersion(&drv_ver);
+    g_tool_tag = "nvrtc" + std::to_string(vmaj) + "." + std::to_string(vmin) + "|driver" + std::to_string(drv_ver);
     g_loaded = true;
     return true;
 }
@@ -804,10 +813,11 @@ qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<
 
 namespace {
 
-// FNV-1a over the source and the target: the name of a cached cubin.
+// FNV-1a over the source, the target and the NVRTC / driver versions: the
+// name of a cached cubin (a cubin from another toolkit gets another name).
 std::string source_key(const std::string &src, const std::string &arch) {
     uint64_t h = 1469598103934665603ull;
-    for (unsigned char c : src + "|" + arch) {
+    for (unsigned char c : src + "|" + arch + "|" + g_tool_tag) {
         h ^= c;
         h *= 1099511628211ull;
     }
@@ -901,7 +911,7 @@ qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<T
     std::vector<std::string> keys(np), logs(np);
     std::vector<char> need(np, 0);
     for (size_t pi = 0; pi < np; ++pi) {
-        if (srcs[pi].empty() || g_modules.count(srcs[pi])) continue;
+        if (srcs[pi].empty() || g_modules.count({dev, srcs[pi]})) continue;
         keys[pi] = source_key(srcs[pi], arch);
         if (!dir.empty() && read_file(dir + "/" + keys[pi] + ".cubin", cubins[pi])) continue;
         need[pi] = 1;
@@ -924,16 +934,26 @@ qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<T
             return set_error(QF_ERR_CUDA, "NVRTC compile of a tile pass failed: " + logs[pi].substr(0, 2000));
         }
         CUmodule mod = nullptr;
-        auto it = g_modules.find(srcs[pi]);
+        auto it = g_modules.find({dev, srcs[pi]});
         if (it != g_modules.end()) {
             mod = it->second;
         } else {
-            const CUresult lr = g_drv.module_load(&mod, cubins[pi].data());
+            CUresult lr = g_drv.module_load(&mod, cubins[pi].data());
+            if (lr != CUDA_SUCCESS && !need[pi]) {
+                // a cached cubin this driver rejects: compile afresh and
+                // replace the cache entry
+                if (!nvrtc_compile(srcs[pi], arch, cubins[pi], logs[pi])) {
+                    delete jp;
+                    return set_error(QF_ERR_CUDA, "NVRTC compile of a tile pass failed: " + logs[pi].substr(0, 2000));
+                }
+                need[pi] = 1;
+                lr = g_drv.module_load(&mod, cubins[pi].data());
+            }
             if (lr != CUDA_SUCCESS) {
                 delete jp;
                 return set_error(QF_ERR_CUDA, "loading a compiled tile pass failed: " + cuda_err(lr));
             }
-            g_modules[srcs[pi]] = mod;
+            g_modules[{dev, srcs[pi]}] = mod;
             if (need[pi] && !dir.empty()) write_file(dir + "/" + keys[pi] + ".cubin", cubins[pi]);
         }
         JitPassInfo &ji = jp->passes[pi];

@@ -55,9 +55,10 @@ def test_noalloc_rejects_bad_arguments():
            (st.tensor.data_ptr(), d, n, qf.QF_C64, 0),                # NULL output
            (st.tensor.data_ptr() + 8, d, n, qf.QF_C64, out.data_ptr()),  # misaligned amplitudes
            (st.tensor.data_ptr(), 1, n, qf.QF_C64, out.data_ptr()),   # d < 2
-           (st.tensor.data_ptr(), 2, 63, qf.QF_C64, out.data_ptr())]  # n + 1 > 64: beyond the scratch
+           (st.tensor.data_ptr(), 2, 63, qf.QF_C64, out.data_ptr())]  # d^n above 9e15 amplitudes
     for args in bad:
         with pytest.raises(qf.QFError) as ei:
             qf.qf_expect_number_noalloc(*args)
         assert ei.value.status == qf.QF_ERR_ARG
+    assert "d^n too large" in str(ei.value)
     st.free()
