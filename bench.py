@@ -217,25 +217,105 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------- CPU baseline leg
-def cpu_baseline(budget_s=20.0):
-    """The oracle as it stands on the host cores: gates of the d=3 n=17
-    sequence on a complex128 state until ~budget_s of work."""
+def _err(got, want, tol=None, rel=False):
+    import numpy as np
+    got = np.asarray(got)
+    want = np.asarray(want)
+    e = {"max_abs": float(np.abs(got - want).max()) if want.size else 0.0}
+    if rel:
+        e["max_rel"] = float((np.abs(got - want) / np.maximum(1.0, np.abs(want))).max()) if want.size else 0.0
+    if tol is not None:
+        e["tol"] = tol
+        e["within"] = bool(e["max_abs"] <= tol)
+    return e
+
+
+def cpu_baseline(keep, size=(3, 17)):
+    """The oracle as it stands (complex128, explicit loops, OpenMP over
+    independent amplitude groups) on the host cores, on bounded samples of
+    the workloads, and the error of every GPU result it can check:
+
+    * forward: the whole 200-gate d=3 n=17 sequence on all cores (timed: the
+      line's value), compared amplitude by amplitude with the GPU's complex64
+      and complex128 results of the same sequence; the first two gates again
+      on one thread;
+    * adjoint (d=3 n=14, 10 layers, 560 parameters): the oracle's derivative
+      circuits for 4 parameters and its loss, against the GPU's complex64 and
+      complex128 gradients (timed per parameter, extrapolated to 560);
+    * batched and VQA: sampled circuits' losses and per-sample gradients.
+    Returns (cpu_baseline record, error_vs_oracle record)."""
     import numpy as np
     from oracle import sim
     from paper_2409_17716_gb300 import workloads as W
-    d, n = 3, 17
     cores = os.cpu_count() or 1
-    psi = sim.basis(d, n, 0)
+    sim.set_threads(cores)
+    errors = {}
+    # ---- forward, all cores
+    d, n = size
     ops = W.random_circuit(d, n, N_GATES)
     t0 = time.perf_counter()
-    g = 0
-    while g < N_GATES and (time.perf_counter() - t0) < budget_s:
-        t, U = sim.op_matrix(ops[g], d)
-        sim.apply(psi, d, n, t, U)
-        g += 1
+    psi = sim.run(ops, d, n)
     dt = time.perf_counter() - t0
-    return {"value": g * d ** n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d gates of the d=3 n=17 sequence, complex128 oracle, %.1f s" % (g, dt)}
+    value = N_GATES * d ** n / dt
+    fw = keep.get("forward")
+    if fw:
+        for dtype, tol in (("c64", 1e-5), ("c128", 1e-12)):
+            got = fw[dtype]
+            m = 0.0
+            for i in range(0, psi.size, 1 << 24):
+                m = max(m, float(np.abs(got[i:i + (1 << 24)].astype(np.complex128) - psi[i:i + (1 << 24)]).max()))
+            errors["forward_" + dtype] = {"max_abs": m, "tol": tol, "within": m <= tol,
+                                          "sample": "the whole 200-gate d=%d n=%d sequence, every amplitude" % (d, n)}
+    del psi
+    # ---- the first two gates on one thread
+    sim.set_threads(1)
+    one = sim.basis(d, n, 0)
+    t0 = time.perf_counter()
+    for op in ops[:2]:
+        t, U = sim.op_matrix(op, d)
+        sim.apply(one, d, n, t, U)
+    dt1 = time.perf_counter() - t0
+    sim.set_threads(cores)
+    del one
+    record = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+              "sample": "the whole 200-gate d=%d n=%d sequence, complex128 oracle, all host cores, %.1f s" % (d, n, dt),
+              "one_thread": {"value": 2 * d ** n / dt1, "unit": UNIT, "cores": 1,
+                             "sample": "first 2 gates of the d=%d n=%d sequence, %.1f s" % (d, n, dt1)}}
+    # ---- adjoint: derivative circuits for a parameter subset
+    adj = keep.get("adjoint")
+    if adj:
+        d, n, ops, theta, w, slots = adj["d"], adj["n"], adj["ops"], adj["theta"], adj["w"], adj["slots"]
+        t0 = time.perf_counter()
+        want_g = sim.grad_bruteforce(ops, d, n, theta, w, slots=slots)
+        tg = time.perf_counter() - t0
+        want_l = sim.loss(sim.run(ops, d, n, params=theta), d, n, w)
+        for dtype in ("c64", "c128"):
+            if dtype in adj:
+                loss, g = adj[dtype]
+                e = _err(g[slots], want_g, 1e-10 if dtype == "c128" else None, rel=True)
+                e["loss_abs"] = abs(loss - want_l)
+                e["sample"] = "d=3 n=14 L=10 ansatz, parameters %s of 560 and the loss" % (slots,)
+                errors["adjoint_" + dtype] = e
+        record["adjoint_bruteforce"] = {
+            "seconds_for_sample": tg, "params_in_sample": len(slots),
+            "seconds_per_gradient_extrapolated": tg / len(slots) * adj["P"],
+            "note": "oracle derivative circuits, all cores; extrapolated linearly to all %d parameters" % adj["P"]}
+    # ---- batched and VQA samples
+    for key in ("batched", "vqa"):
+        smp = keep.get(key)
+        if not smp:
+            continue
+        t0 = time.perf_counter()
+        eg, el, worst_rel = 0.0, 0.0, 0.0
+        for c_ops, cd, cn, slots, loss_gpu, g_gpu, params in smp["circuits"]:
+            w = [1.0] + [0.0] * (cn - 1)
+            want = sim.grad_bruteforce(c_ops, cd, cn, params, w, slots=slots)
+            wl = sim.loss(sim.run(c_ops, cd, cn, params=params), cd, cn, w)
+            eg = max(eg, float(np.abs(np.asarray(g_gpu) - want).max()) if len(slots) else 0.0)
+            el = max(el, abs(loss_gpu - wl))
+        errors[key + "_" + smp["dtype"]] = {"max_abs": eg, "loss_abs": el, "sample": smp["sample"]}
+        record[key + "_oracle_seconds"] = time.perf_counter() - t0
+    return record, errors
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -351,17 +431,25 @@ def main():
         qf.qf_program_free(p)
     for st in states:
         st.free()
+    keep = {}   # GPU outputs the oracle checks in the CPU-baseline leg
     if extras:
         torch.cuda.empty_cache()
-        line["adjoint"] = adjoint_bench(qf, W, torch, hbm_peak)
+        keep["forward"] = forward_outputs(qf, W, torch)
         torch.cuda.empty_cache()
-        line["batched"] = batch_bench(qf, W, torch)
+        line["adjoint"] = adjoint_bench(qf, W, torch, hbm_peak, keep)
         torch.cuda.empty_cache()
-        line["vqa_training"] = vqa_bench(qf, W, torch)
+        line["batched"] = batch_bench(qf, W, torch, keep)
+        torch.cuda.empty_cache()
+        line["vqa_training"] = vqa_bench(qf, W, torch, keep)
         torch.cuda.empty_cache()
         line["mixed_dims"] = mixed_bench(qf, W, torch, hbm_peak)
     if extras and rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"], errors = cpu_baseline(keep)
+        line["error_vs_oracle"] = errors
+        for leg, key in (("adjoint", "adjoint"), ("batched", "batched"), ("vqa_training", "vqa")):
+            if leg in line:
+                line[leg]["error_vs_oracle"] = {k: v for k, v in errors.items() if k.startswith(key)}
+        line["c128"]["error_vs_oracle"] = errors.get("forward_c128")
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -379,6 +467,23 @@ def _time_ms(torch, fn, reps=3):
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
+
+
+def forward_outputs(qf, W, torch, d=3, n=17):
+    """The d=3 n=17 benchmark sequence run once from |0...0> through the
+    timed fused program in complex64 and complex128; host copies of the final
+    states for the oracle comparison."""
+    ops = W.random_circuit(d, n, N_GATES)
+    p = qf.program_from_ops(d, n, ops, fuse=True)
+    out = {"d": d, "n": n}
+    for dtype in ("c64", "c128"):
+        st = qf.State(d, n, dtype).set_basis(0)
+        qf.qf_program_run(p, st.handle)
+        torch.cuda.synchronize()
+        out[dtype] = st.tensor.cpu().numpy()
+        st.free()
+    qf.qf_program_free(p)
+    return out
 
 
 def per_size_throughput(qf, W, torch, sizes, states, progs, args):
@@ -529,15 +634,56 @@ def mixed_bench(qf, W, torch, hbm_peak):
     return out
 
 
-def adjoint_bench(qf, W, torch, hbm_peak):
+ADJ_N14_SLOTS = [3, 150, 297, 559]     # oracle-checked parameters of the d=3 n=14 L=10 ansatz
+ADJ_N20_FD_SLOTS = [47, 141, 235, 319]  # central-difference parameters of the d=3 n=20 L=4 ansatz
+
+
+def central_differences_c128(qf, torch, d, n, ops, theta, w, slots, h=1e-5):
+    """FP64 central differences of sum_q w_q <N_q> from complex128 forward
+    runs on this GPU.  One state advances through the circuit; at each
+    chosen parameter a copy runs the remaining gates at theta +- h."""
+    import numpy as np
+    pos = {op.param: l for l, op in enumerate(ops) if op.param >= 0}
+    a, b = qf.State(d, n, "c128").set_basis(0), qf.State(d, n, "c128")
+    prev, fd = 0, {}
+    for s in sorted(slots, key=lambda x: pos[x]):
+        l = pos[s]
+        if l > prev:
+            seg = qf.program_from_ops(d, n, ops[prev:l])
+            qf.qf_program_run(seg, a.handle, theta)
+            qf.qf_program_free(seg)
+            prev = l
+        suf = qf.program_from_ops(d, n, ops[l:])
+        vals = []
+        for sign in (1.0, -1.0):
+            b.tensor.copy_(a.tensor)
+            t = np.array(theta, dtype=float)
+            t[s] += sign * h
+            qf.qf_program_run(suf, b.handle, t)
+            vals.append(float(np.dot(w, b.expect_number()[:n])))
+        qf.qf_program_free(suf)
+        fd[s] = (vals[0] - vals[1]) / (2 * h)
+    a.free()
+    b.free()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return fd
+
+
+def adjoint_bench(qf, W, torch, hbm_peak, keep):
     """Full gradient (forward + adjoint) of the variational ansatz vs the
-    forward + central-difference path on the same GPU (2P + 1 forwards)."""
+    forward + central-difference path on the same GPU (2P + 1 forwards).
+    The d=3 n=14 gradients are kept for the oracle; the d=3 n=20 complex64
+    gradient is checked against complex128 central differences here."""
+    import numpy as np
     out = {}
     cases = [("d3_n14_L10", 3, 14, 10, ("c64", "c128")), ("d3_n20_L4", 3, 20, 4, ("c64",))]
     for name, d, n, L, dtypes in cases:
         ops, P = W.variational_ansatz(d, n, L, entangler="ring" if n == 14 else "chain")
         theta = W.normal_angles(P, seed=n)
         w = [1.0] * n
+        if n == 14:
+            keep["adjoint"] = {"d": d, "n": n, "ops": ops, "theta": theta, "w": w, "P": P, "slots": ADJ_N14_SLOTS}
         for dtype in dtypes:
             p = qf.program_from_ops(d, n, ops)
             psi, lam = qf.State(d, n, dtype), qf.State(d, n, dtype)
@@ -575,15 +721,29 @@ def adjoint_bench(qf, W, torch, hbm_peak):
                 "passes_forward": fwd_passes, "passes_adjoint": adj_passes,
                 "hbm_gbs": by / (t_g / 1e3) / 1e9, "hbm_frac": by / (t_g / 1e3) / 1e9 / hbm_peak,
                 "note": "fd = (2P+1) forward runs of the same fused program on this GPU"}
+            torch.cuda.synchronize()
+            g_host = grad.cpu().numpy().copy()
+            l_host = float(loss.item())
+            if n == 14:
+                keep["adjoint"][dtype] = (l_host, g_host)
             qf.qf_program_free(p)
             psi.free()
             lam.free()
             del ev, grad, loss
             torch.cuda.empty_cache()
+            if n == 20:
+                t0 = time.perf_counter()
+                fd = central_differences_c128(qf, torch, d, n, ops, theta, w, ADJ_N20_FD_SLOTS)
+                fd_v = np.array([fd[s] for s in ADJ_N20_FD_SLOTS])
+                e = _err(g_host[ADJ_N20_FD_SLOTS], fd_v, rel=True)
+                e["reference"] = ("FP64 central differences (h=1e-5) of the complex128 forward on this GPU, "
+                                  "parameters %s of %d" % (ADJ_N20_FD_SLOTS, P))
+                e["seconds"] = time.perf_counter() - t0
+                out[name + "_" + dtype]["error_vs_c128_fd"] = e
     return out
 
 
-def batch_bench(qf, W, torch):
+def batch_bench(qf, W, torch, keep):
     """4096 circuits (d 2..5, n 4..10, L 2..6), forward + adjoint in one graph
     replay, vs per-circuit forward + central differences on the same GPU
     (sampled over 64 circuits and extrapolated)."""
@@ -608,6 +768,21 @@ def batch_bench(qf, W, torch):
     qf.qf_batch_run(b, params, True)
     t_fb = _time_ms(torch, lambda: qf.qf_batch_run(b, params, True), reps=3)
     t_f = _time_ms(torch, lambda: qf.qf_batch_run(b, params, False), reps=3)
+    # outputs of a forward + backward run for the oracle: 8 circuits of at
+    # most 4096 amplitudes drawn from the batch
+    qf.qf_batch_run(b, params, True)
+    loss_all, gl_all, _ = qf.qf_batch_read(b)
+    rs = np.random.default_rng(2)
+    small = [i for i, c in enumerate(circuits) if c.d ** c.n <= 4096]
+    picks = [int(i) for i in rs.choice(small, min(8, len(small)), replace=False)]
+    smp = []
+    for i in picks:
+        c = circuits[i]
+        slots, off = qf.qf_batch_circuit_params(b, i)
+        smp.append((c.ops, c.d, c.n, slots, float(loss_all[i]), gl_all[off:off + len(slots)].copy(), params))
+    keep["batched"] = {"dtype": "c64", "circuits": smp,
+                       "sample": "circuits %s of the 4096 (those with at most 4096 amplitudes, drawn at random): "
+                                 "loss and every parameter's gradient" % picks}
     # per-circuit forward + FD baseline on a sample
     rng = np.random.default_rng(1)
     sample = rng.choice(len(circuits), 64, replace=False)
@@ -640,7 +815,7 @@ def batch_bench(qf, W, torch):
             "note": "fd baseline: per-circuit fused forward + <N_q> on this GPU, (2P_c+1) runs, 64-circuit sample"}
 
 
-def vqa_bench(qf, W, torch):
+def vqa_bench(qf, W, torch, keep):
     """Training-step throughput of the paper's VQA circuits (rotation blocks
     R1 / R2 / R3): 4096 samples per step (Iris-like d=3 n=4, MNIST-like d=10
     n=2 and n=4), forward + adjoint of <N_0> in one graph replay, complex64."""
@@ -658,6 +833,16 @@ def vqa_bench(qf, W, torch):
             qf.qf_batch_run(b, params, True)
             ms = _time_ms(torch, lambda: qf.qf_batch_run(b, params, True), reps=3)
             info = qf.qf_batch_info(b)
+            if (d, n, variant) in ((3, 4, "R1"), (10, 2, "R3")):
+                loss_all, gl_all, _ = qf.qf_batch_read(b)
+                smp = keep.setdefault("vqa", {"dtype": "c64", "circuits": [],
+                                              "sample": "samples 0, 1000, 2000, 4095 of the d=3 n=4 R1 and d=10 n=2 "
+                                                        "R3 steps: loss and every parameter's gradient"})
+                for i in (0, 1000, 2000, 4095):
+                    c = circuits[i]
+                    slots, off = qf.qf_batch_circuit_params(b, i)
+                    smp["circuits"].append((c.ops, c.d, c.n, slots, float(loss_all[i]),
+                                            gl_all[off:off + len(slots)].copy(), params))
             out["d%d_n%d_%s" % (d, n, variant)] = {
                 "samples_per_s": 4096 / (ms / 1e3), "step_ms": ms, "gates": len(circuits[0].ops),
                 "gradients_per_s": info["grad_local_len"] / (ms / 1e3)}

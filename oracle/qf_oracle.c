@@ -37,6 +37,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <omp.h>
 
 typedef double complex cplx;
 
@@ -533,4 +534,16 @@ void or_basis_state(cplx *psi, long long N, long long index)
 {
     for (long long i = 0; i < N; ++i) psi[i] = 0.0;
     psi[index] = 1.0;
+}
+
+/* Host threads the OpenMP loops use (the CPU baseline times the oracle on
+ * all host cores and on one); no arithmetic changes with the count. */
+void or_set_threads(int t)
+{
+    omp_set_num_threads(t > 0 ? t : 1);
+}
+
+int or_get_threads(void)
+{
+    return omp_get_max_threads();
 }

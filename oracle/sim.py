@@ -74,8 +74,19 @@ def lib():
         L.or_marginal.argtypes = [_cp, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _cp]
         L.or_inner.argtypes = [_cp, _cp, _c.c_longlong, _cp, _cp]
         L.or_basis_state.argtypes = [_cp, _c.c_longlong, _c.c_longlong]
+        L.or_set_threads.argtypes = [_c.c_int]
+        L.or_get_threads.restype = _c.c_int
         _LIB = L
     return _LIB
+
+
+def set_threads(t: int) -> None:
+    """Host threads of the oracle's OpenMP loops (results do not depend on it)."""
+    lib().or_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def _ptr(a: np.ndarray):
@@ -301,23 +312,26 @@ def grad_bruteforce(ops, d, n: int, params, weights, psi0=None, slots=None) -> n
     """dL/dtheta_p for L = sum_q w_q <N_q>, by explicit derivative circuits."""
     params = np.asarray(params, dtype=float)
     P = len(params)
-    slots = range(P) if slots is None else slots
+    slots = list(range(P) if slots is None else slots)
     start = basis(d, n, 0) if psi0 is None else np.array(psi0, dtype=np.complex128)
-    # prefix states: prefix[l] = state before gate l
-    prefix = [start.copy()]
-    cur = start.copy()
-    for op in ops:
-        t, U = op_matrix(op, d, params)
-        apply(cur, d, n, t, U)
-        prefix.append(cur.copy())
-    final = cur
-    Odiag = number_weights_diag(d, n, weights)
-    O_psi = Odiag * final
     uses = {}
     for l, op in enumerate(ops):
         if op.kind in ("rot", "crot") and op.param >= 0:
             uses.setdefault(op.param, []).append(l)
-    g = np.zeros(len(list(slots)) if not isinstance(slots, range) else len(slots))
+    # prefix[l] = state before gate l, kept only for the gates of the
+    # requested slots (the full list would hold one state per gate)
+    need = {l for p in slots for l in uses.get(p, [])}
+    prefix = {}
+    cur = start.copy()
+    for l, op in enumerate(ops):
+        if l in need:
+            prefix[l] = cur.copy()
+        t, U = op_matrix(op, d, params)
+        apply(cur, d, n, t, U)
+    final = cur
+    Odiag = number_weights_diag(d, n, weights)
+    O_psi = Odiag * final
+    g = np.zeros(len(slots))
     for out_i, p in enumerate(slots):
         dpsi = np.zeros_like(final)
         for l in uses.get(p, []):

@@ -90,9 +90,18 @@ def test_batch_matches_single_circuits(orc, dtype):
         qf.qf_program_free(p)
 
 
+def _spread(slots, k=4):
+    """k slots spread over a circuit's parameters (first, last, between)."""
+    if len(slots) <= k:
+        return list(slots)
+    return [slots[int(round(i * (len(slots) - 1) / (k - 1)))] for i in range(k)]
+
+
 def test_batch_full_size_sample(orc):
-    """The 4096-circuit workload (d 2..5, n 4..10, L 2..6) in complex64: a
-    sample of circuits against the same circuit run alone."""
+    """The 4096-circuit workload (d 2..5, n 4..10, L 2..6) in complex64: 16
+    circuits drawn at random against the same circuit run alone (every
+    parameter) and against the oracle (loss, and the derivative circuits of
+    4 parameters per circuit: first, last and two between)."""
     qf = gpu_lib()
     circuits, params = W.batch_circuits(count=4096)
     w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
@@ -112,6 +121,12 @@ def test_batch_full_size_sample(orc):
         lam.free()
         assert abs(loss[i] - l1) <= 2e-6
         assert np.abs(gl[off:off + len(slots)] - g1[slots]).max() <= 2e-5
+        sub = _spread(slots)
+        want = orc.grad_bruteforce(c.ops, c.d, c.n, params, w0(c), slots=sub)
+        got = np.array([gl[off + slots.index(s_)] for s_ in sub])
+        assert np.abs(got - want).max() <= 2e-5, (int(i), np.abs(got - want).max())
+        wl = orc.loss(orc.run(c.ops, c.d, c.n, params=params), c.d, c.n, w0(c))
+        assert abs(loss[i] - wl) <= 2e-6
     assert np.isfinite(gs).all()
     qf.qf_batch_free(b)
     for p in progs:
@@ -168,6 +183,34 @@ def test_vqa_batch_vs_oracle(orc, variant, d, n):
         assert np.abs(gl[off:off + len(slots)] - want).max() <= 1e-10
         wl = orc.loss(orc.run(c.ops, d, n, params=params), d, n, w0(c))
         assert abs(loss[i] - wl) <= 1e-12
+    qf.qf_batch_free(b)
+    for p in progs:
+        qf.qf_program_free(p)
+
+
+def test_batch_workload_prefix_c128_vs_oracle(orc):
+    """The first 256 circuits of the 4096-circuit workload (same generator,
+    n up to 10) batched in complex128: 16 of them, drawn at random, against
+    the oracle -- loss within 1e-12, the derivative circuits of 4 parameters
+    per circuit within 1e-10."""
+    qf = gpu_lib()
+    circuits, params = W.batch_circuits(count=4096)
+    circuits = circuits[:256]
+    assert max(c.n for c in circuits) == 10
+    w0 = lambda c: [1.0] + [0.0] * (c.n - 1)
+    b, progs = make_batch(qf, circuits, params, "c128", w0)
+    qf.qf_batch_run(b, params, True)
+    loss, gl, _ = qf.qf_batch_read(b)
+    rng = np.random.default_rng(4)
+    for i in rng.choice(len(circuits), 16, replace=False):
+        c = circuits[i]
+        slots, off = qf.qf_batch_circuit_params(b, int(i))
+        sub = _spread(slots)
+        want = orc.grad_bruteforce(c.ops, c.d, c.n, params, w0(c), slots=sub)
+        got = np.array([gl[off + slots.index(s_)] for s_ in sub])
+        assert np.abs(got - want).max() <= 1e-10, (int(i), np.abs(got - want).max())
+        wl = orc.loss(orc.run(c.ops, c.d, c.n, params=params), c.d, c.n, w0(c))
+        assert abs(loss[i] - wl) <= 1e-12, (int(i), loss[i], wl)
     qf.qf_batch_free(b)
     for p in progs:
         qf.qf_program_free(p)

@@ -146,3 +146,21 @@ def test_invalid_apply(orc):
         orc.apply(psi, 3, 3, [0, 0], np.eye(9))
     with pytest.raises(ValueError):
         orc.apply(psi, 3, 3, [3], np.eye(3))
+
+
+def test_thread_count_does_not_change_results(orc):
+    """The CPU baseline times the oracle on one thread and on all cores; the
+    amplitudes must be bit-identical either way (OpenMP only splits
+    independent amplitude groups)."""
+    from paper_2409_17716_gb300 import workloads as W
+    d, n = 3, 8
+    ops = W.random_circuit(d, n, 40)
+    before = orc.get_threads()
+    try:
+        orc.set_threads(1)
+        one = orc.run(ops, d, n)
+        orc.set_threads(4)
+        many = orc.run(ops, d, n)
+    finally:
+        orc.set_threads(before)
+    assert np.array_equal(one, many)
