@@ -477,6 +477,57 @@ static bool single_qudit_gate(const HGate &g) {
     return g.nq == 1 && (g.kind == G_H || g.kind == G_X || g.kind == G_Z || g.kind == G_ROT || g.kind == G_DENSE);
 }
 
+static bool gate_is_diagonal(const HGate &g) {
+    return g.kind == G_Z || (g.kind == G_ROT && (g.axis == 'z' || g.axis == 'g'));
+}
+
+// Levels a diagonal gate changes (bit l set: level l gets a phase != 1 in
+// general).
+static int diag_levels(const HGate &g, int d) {
+    int m = 0;
+    if (g.kind == G_Z) {
+        for (int l = 0; l < d; ++l)
+            if (((long long)g.power * l) % d != 0) m |= 1 << l;
+    } else if (g.axis == 'z') {
+        m = (1 << g.j) | (1 << g.k);
+    } else {   // Gell-Mann diagonal j: levels 0..j
+        m = (1 << (g.j + 1)) - 1;
+    }
+    return m;
+}
+
+static int popcount_i(int x) {
+    int c = 0;
+    for (; x; x &= x - 1) ++c;
+    return c;
+}
+
+// Arithmetic of a single-qudit gate applied alone, per fibre of d
+// amplitudes, in paired-FMA issue slots: a complex multiply(-add) is two, a
+// real one is one.  Dense: d outputs of d complex terms; RX pair: two outputs
+// of two complex terms; RY pair: real entries; diagonal: one complex
+// multiply per changed level; shift: a permutation, free.
+static int gate_cost(const HGate &g, int d) {
+    switch (g.kind) {
+    case G_H:
+    case G_DENSE: return 2 * d * d;
+    case G_X: return 0;
+    case G_Z: return 2 * popcount_i(diag_levels(g, d));
+    case G_ROT:
+        if (g.axis == 'x') return 8;
+        if (g.axis == 'y') return 4;
+        return 2 * popcount_i(diag_levels(g, d));
+    default: return 2 * d * d;
+    }
+}
+
+// Cost of a group of diagonal gates merged into one diagonal.
+static int diag_cost(const std::vector<HGate> &gates, const std::vector<int> &grp, int d) {
+    int m = 0;
+    for (int gi : grp) m |= diag_levels(gates[gi], d);
+    return 2 * popcount_i(m);
+}
+
 // Which rL (largest) lets the qudit set fit nt_max local qudits; -1 if none.
 static int fit_rl(const std::vector<bool> &inset, int n, int nt_max, int rl_min) {
     int top = std::min(nt_max, n);
@@ -521,23 +572,74 @@ std::vector<PassPlan> plan_passes(const std::vector<HGate> &gates, int d, int n,
         std::vector<int> active;
         for (int q = 0; q < n - rL; ++q)
             if (inset[q]) active.push_back(q);
-        // group consecutive single-qudit gates on the same qudit
-        std::vector<int> last_op_on(n, -1);  // op index touching qudit last
+        // Group single-qudit gates on the same qudit.  A qudit's run of
+        // consecutive single-qudit gates (no multi-qudit gate on it in
+        // between; gates on other qudits commute with them) becomes one op
+        // where that costs no more arithmetic: diagonal gates merge into one
+        // diagonal, and the run becomes one dense d x d product once it holds
+        // a dense gate or once its ops applied one by one would cost at least
+        // a dense product (gate_cost); otherwise its gates stay separate ops.
+        // Qubit runs always merge: a 2 x 2 product costs at most two cheap
+        // ops, and the separate ops measured 10 % slower (an extra register
+        // stage in the heaviest pass of the n=28 program).
+        std::vector<int> last_op_on(n, -1);            // op index touching qudit last
+        std::vector<std::vector<int>> chain(n);        // the qudit's open single-qudit ops
+        std::vector<char> gdense, gdiag;               // per op: dense product / diagonal
+        std::vector<int> gcost;                        // per op: cost applied alone
+        const int dense_cost = d == 2 ? 0 : 2 * d * d;
+        auto new_group = [&](int gi, bool dense, bool diag, int cost) {
+            p.groups.push_back({gi});
+            gdense.push_back(dense);
+            gdiag.push_back(diag);
+            gcost.push_back(cost);
+            return (int)p.groups.size() - 1;
+        };
         for (int gi : members) {
             const HGate &g = gates[gi];
             // the adjoint needs every parametrised gate as an op of its own
-            const bool mergeable = !for_adjoint || !gate_is_param(g);
-            if (fuse && mergeable && single_qudit_gate(g) && last_op_on[g.q[0]] >= 0) {
-                std::vector<int> &grp = p.groups[last_op_on[g.q[0]]];
-                const HGate &g0 = gates[grp[0]];
-                if (single_qudit_gate(g0) && (!for_adjoint || !gate_is_param(g0))) {
-                    grp.push_back(gi);
-                    continue;
+            const bool mergeable = fuse && single_qudit_gate(g) && (!for_adjoint || !gate_is_param(g));
+            if (!mergeable) {
+                const int ix = new_group(gi, false, false, 0);
+                for (int i = 0; i < g.nq; ++i) {
+                    last_op_on[g.q[i]] = ix;
+                    chain[g.q[i]].clear();
                 }
+                continue;
             }
-            p.groups.push_back({gi});
-            for (int i = 0; i < g.nq; ++i) last_op_on[g.q[i]] = (int)p.groups.size() - 1;
+            const int q = g.q[0];
+            std::vector<int> &ch = chain[q];
+            const bool g_dense = g.kind == G_H || g.kind == G_DENSE;
+            const bool g_diag = gate_is_diagonal(g);
+            const int g_cost = gate_cost(g, d);
+            const int last = ch.empty() ? -1 : ch.back();
+            if (last >= 0 && (gdense[last] || (g_diag && gdiag[last]))) {
+                p.groups[last].push_back(gi);   // into a dense product, or diagonal into diagonal
+                if (!gdense[last]) gcost[last] = diag_cost(gates, p.groups[last], d);
+                continue;
+            }
+            const int ix = new_group(gi, g_dense, g_diag, g_dense ? dense_cost : g_cost);
+            last_op_on[q] = ix;
+            ch.push_back(ix);
+            int total = 0;
+            for (int c : ch) total += gcost[c];
+            if (ch.size() > 1 && (g_dense || total >= dense_cost)) {
+                // one dense product at the chain's first op (the gates in
+                // between touch other qudits only)
+                const int first = ch[0];
+                for (size_t i = 1; i < ch.size(); ++i) {
+                    for (int m : p.groups[ch[i]]) p.groups[first].push_back(m);
+                    p.groups[ch[i]].clear();
+                }
+                gdense[first] = 1;
+                gdiag[first] = 0;
+                gcost[first] = dense_cost;
+                ch.assign(1, first);
+                last_op_on[q] = first;
+            }
         }
+        p.groups.erase(std::remove_if(p.groups.begin(), p.groups.end(),
+                                      [](const std::vector<int> &x) { return x.empty(); }),
+                       p.groups.end());
         // a lone gate on one wide target goes through the strided kernel
         if (!for_adjoint && p.groups.size() == 1 && p.groups[0].size() == 1) {
             const HGate &g = gates[p.groups[0][0]];

@@ -195,7 +195,21 @@ struct PassSrc {
     int ncols = 0;       // gradient columns (parametrised ops, op.gcol) of an adjoint pass
     std::vector<TOp> ops;
     std::vector<TStage> stages;
+    // Padded tile layout (forward complex64 passes at odd d, runs of >= 3
+    // amplitudes): every run of SEG amplitudes sits in a slot of SEG + 1,
+    // shifted by one where it starts at an odd amplitude, so that each run
+    // moves between HBM and shared memory as 16-byte amplitude pairs.  A run
+    // of an odd-d state starts at an odd index exactly when its run number
+    // plus the tile base is odd (every stride is odd).
+    bool pad = false;
+    int slots() const { return pad ? (T / SEG) * (SEG + 1) : T; }   // amplitudes of one tile buffer
 };
+
+// Whether a forward pass of this geometry uses the padded tile layout: runs
+// of at least 9 amplitudes (measured on GB300: d=3 passes 3.5 % faster; at
+// d=5 with 5-amplitude runs the 20 % larger tile costs the second buffer and
+// the passes ran 17 % slower).
+static bool use_pad(int d, bool c128, bool adj, int SEG) { return !c128 && !adj && d % 2 == 1 && SEG >= 9; }
 
 class Gen {
   public:
@@ -219,7 +233,7 @@ class Gen {
         o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
         o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm);\n";
         o_ << "  C *buf0 = reinterpret_cast<C *>(qj_sm + " << boff << ");\n";
-        o_ << "  C *buf1 = buf0 + " << p_.T << ";\n";
+        o_ << "  C *buf1 = buf0 + " << p_.slots() << ";   // tile of " << p_.T << " amplitudes\n";
         o_ << "  const int tid = threadIdx.x;\n";
         o_ << "  const bool db = A.mode != 0;\n";
         emit_offA(NA);
@@ -238,6 +252,7 @@ class Gen {
         transfer(true, {{"tile", "A.psi"}});
         o_ << "      qj_commit();\n      qj_wait0();\n    }\n";
         o_ << "    __syncthreads();\n";
+        if (p_.pad) o_ << "    const int tp = (int)(base & 1);\n";
         for (const TStage &st : p_.stages) {
             if (st.legacy) legacy(p_.ops[st.first]);
             else stage(st);
@@ -245,6 +260,37 @@ class Gen {
         }
         transfer(false, {{"tile", "A.psi"}});
         o_ << "    __syncthreads();\n  }\n  qj_wait0();\n}\n";
+    }
+
+    // Padded layout: run a of the tile fills the 16-byte aligned window of
+    // SEG + 1 amplitudes that starts at (base + offA[a]) rounded down to an
+    // even index, i.e. chunk k = a * CH + c of CH = (SEG + 1) / 2 amplitude
+    // pairs lands at slot 2k.  The chunk holding only the run's first (odd
+    // start) or last (even start) amplitude moves that amplitude alone, so
+    // nothing outside the run is read or written.
+    void transfer_pad(bool load) {
+        const int NA = p_.T / p_.SEG, CH = (p_.SEG + 1) / 2;
+        auto body = [&](const std::string &a, const std::string &c, const std::string &k) {
+            o_ << "const long long rs = base + offA[" << a << "]; const int sh = (int)(rs & 1); "
+               << "const long long g = rs - sh + 2 * " << c << "; C *dst = tile + 2 * (" << k << "); ";
+            if (load)
+                o_ << "if (" << c << " == 0 && sh) qj_cp(dst + 1, A.psi + g + 1); else if (" << c << " == " << CH - 1
+                   << " && !sh) qj_cp(dst, A.psi + g); else qj_cp2(dst, A.psi + g); ";
+            else
+                o_ << "if (" << c << " == 0 && sh) A.psi[g + 1] = dst[1]; else if (" << c << " == " << CH - 1
+                   << " && !sh) A.psi[g] = dst[0]; else qj_st2(A.psi + g, dst); ";
+        };
+        if (CH >= 64) {
+            o_ << "    for (int a = 0; a < " << NA << "; ++a) {\n      for (int c = tid; c < " << CH << "; c += "
+               << p_.threads << ") { ";
+            body("a", "c", "a * " + std::to_string(CH) + " + c");
+            o_ << "}\n    }\n";
+        } else {
+            o_ << "    for (int k = tid; k < " << NA * CH << "; k += " << p_.threads << ") { const int a = k / " << CH
+               << "; const int c = k - a * " << CH << "; ";
+            body("a", "c", "k");
+            o_ << "}\n";
+        }
     }
 
     // offA[a] = offset of run a: digits of a on the active qudits (literal strides).
@@ -332,6 +378,10 @@ class Gen {
     // amplitude pairs (every run start is even, so 16-byte aligned); runs of
     // at least 64 transfers are walked run by run without index division.
     void transfer(bool load, const std::vector<std::pair<std::string, std::string>> &bufs) {
+        if (p_.pad) {
+            transfer_pad(load);
+            return;
+        }
         const int pf = (!p_.c128 && D_ % 2 == 0 && p_.SEG % 2 == 0) ? 2 : 1;
         const int per_run = p_.SEG / pf, NA = p_.T / p_.SEG;
         auto one = [&](const std::string &sm, const std::string &g, const std::string &e, const std::string &gi) {
@@ -383,10 +433,33 @@ class Gen {
             for (int i = 0; i < K; ++i) o += ((r / ipow_i(D_, K - 1 - i)) % D_) * st.ls[i];
             off[r] = o;
         }
-        for (int r = 0; r < DK; ++r) o_ << "      C " << V(r) << " = tile[b + " << off[r] << "];\n";
+        std::vector<std::string> at(DK);
+        if (p_.pad) {
+            // b = a_b * SEG + l_b; register r sits Da runs and Dl amplitudes
+            // further (off[r] = Da * SEG + Dl, the stage's digits are zero in
+            // b), at slot (a_b + Da) * (SEG + 1) + l_b + Dl + shift, and the
+            // shift of run a_b + Da is the block's shift flipped when Da is odd
+            const int SEG = p_.SEG;
+            o_ << "      const int ab = b / " << SEG << "; const int sb = (tp ^ ab) & 1;\n";
+            o_ << "      C *P0 = tile + b + ab + sb; C *P1 = tile + b + ab + 1 - sb;\n";
+            for (int r = 0; r < DK; ++r) {
+                const int da = off[r] / SEG, dl = off[r] % SEG;
+                at[r] = std::string(da & 1 ? "P1[" : "P0[") + std::to_string(da * (SEG + 1) + dl) + "]";
+            }
+        } else {
+            for (int r = 0; r < DK; ++r) at[r] = "tile[b + " + std::to_string(off[r]) + "]";
+        }
+        for (int r = 0; r < DK; ++r) o_ << "      C " << V(r) << " = " << at[r] << ";\n";
         for (int i = 0; i < st.nops; ++i) op(p_.ops[st.first + i]);
-        for (int r = 0; r < DK; ++r) o_ << "      tile[b + " << off[r] << "] = " << V(r) << ";\n";
+        for (int r = 0; r < DK; ++r) o_ << "      " << at[r] << " = " << V(r) << ";\n";
         o_ << "    }\n";
+    }
+
+    // Shared-memory element of standard tile index e (legacy ops).
+    std::string sx(const std::string &e) const {
+        if (!p_.pad) return e;
+        const std::string S = std::to_string(p_.SEG);
+        return "(" + e + " + " + e + " / " + S + " + ((tp ^ (" + e + " / " + S + ")) & 1))";
     }
 
     void stage_adj(const TStage &st) {
@@ -640,8 +713,9 @@ class Gen {
             const int la = o.lsa, lc = o.lsc;
             o_ << "    for (int e = tid; e < " << p_.T << "; e += " << p_.threads << ") {\n";
             o_ << "      const int x = (e / " << la << ") % " << D_ << ", y = (e / " << lc << ") % " << D_ << ";\n";
-            o_ << "      if (x < y) { const int e2 = e + (y - x) * " << (la - lc) << "; const C t0 = " << tn_ << "[e]; "
-               << tn_ << "[e] = " << tn_ << "[e2]; " << tn_ << "[e2] = t0; }\n    }\n";
+            o_ << "      if (x < y) { const int e2 = e + (y - x) * " << (la - lc) << "; const C t0 = " << tn_ << "["
+               << sx("e") << "]; " << tn_ << "[" << sx("e") << "] = " << tn_ << "[" << sx("e2") << "]; " << tn_ << "["
+               << sx("e2") << "] = t0; }\n    }\n";
             return;
         }
         // OP_DENSEK: entries always in global memory (up to 64 x 64)
@@ -663,10 +737,10 @@ class Gen {
             o_ << (r ? ", " : "") << off;
         }
         o_ << "};\n      C xs[" << DK << "];\n";
-        o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = " << tn_ << "[b + offs[r]];\n";
+        o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = " << tn_ << "[" << sx("(b + offs[r])") << "];\n";
         o_ << "      for (int r = 0; r < " << DK << "; ++r) { C acc = jm(A.gp[" << o.mat << " + r * " << DK
            << "], xs[0]); for (int x = 1; x < " << DK << "; ++x) acc = jma(A.gp[" << o.mat << " + r * " << DK
-           << " + x], xs[x], acc); " << tn_ << "[b + offs[r]] = acc; }\n    }\n";
+           << " + x], xs[x], acc); " << tn_ << "[" << sx("(b + offs[r])") << "] = acc; }\n    }\n";
     }
 };
 
@@ -734,6 +808,7 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.runS.assign(pp.geom.runS, pp.geom.runS + pp.geom.nruns);
         ps.strideA.assign(pp.geom.strideA, pp.geom.strideA + pp.geom.kA);
         ps.adj = adj;
+        ps.pad = use_pad(d, c128, adj, ps.SEG);
         ps.K = std::min(k_override > 0 ? k_override : (adj ? jit_stage_k_adj(d, c128) : jit_stage_k(d, c128)), pp.geom.nt);
         ps.ops = ops[pi];
         ps.stages = build_stages(ps.ops, pp.geom, d, ps.K);
@@ -785,9 +860,9 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
             ji.smem = (size_t)2 * ps.T * (c128 ? 16 : 8) + (size_t)(ps.T / ps.SEG) * 8;   // psi and lambda tiles
         } else {
             const size_t boff = ((size_t)(ps.T / ps.SEG) * 8 + 15) & ~(size_t)15;
-            ji.smem = boff + (size_t)ps.T * (c128 ? 16 : 8);         // single buffer
-            ji.smem2 = boff + (size_t)2 * ps.T * (c128 ? 16 : 8);    // double buffer
-            ji.l1_copies = !c128 && !(d % 2 == 0 && ps.SEG % 2 == 0);
+            ji.smem = boff + (size_t)ps.slots() * (c128 ? 16 : 8);         // single buffer
+            ji.smem2 = boff + (size_t)2 * ps.slots() * (c128 ? 16 : 8);    // double buffer
+            ji.l1_copies = !c128 && !ps.pad && !(d % 2 == 0 && ps.SEG % 2 == 0);
         }
         ji.ncols = ps.ncols;
         ji.header = adj ? 40 : 24;
