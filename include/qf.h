@@ -287,6 +287,21 @@ qf_status qf_program_set_stage_slots(qf_program *p, int slots);
  * NULL to query the length.  Host only; nothing is compiled or launched. */
 qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, int adjoint, char *buf, size_t cap, size_t *len);
 qf_status qf_program_set_fusion(qf_program *p, int enable);
+/* Arithmetic of the compiled forward passes on complex128 states.  The
+ * state is complex128 either way ("Library Architecture": a state of complex
+ * amplitudes); exact = 0 (the default) computes the gates in double-float
+ * arithmetic on FP32 units -- each real an unevaluated sum of two floats,
+ * products split exactly by a fused multiply-add (Dekker's TwoProduct), sums
+ * by Knuth's TwoSum, about 48 significant bits, within 1e-12 max-abs of the
+ * exact result after the 200-gate benchmark circuits -- converting the state
+ * in place to that form before the first compiled pass and back after the
+ * last (the caller never sees the intermediate form; the stream is the
+ * state's).  exact = 1 computes in FP64 (on GB300 about 1/70 of the FP32
+ * rate).  In the double-float form amplitudes must stay below 2^128 in
+ * magnitude; parts of magnitude 2^-74 .. 2^-126 keep an absolute precision of
+ * 2^-96 and smaller ones become 0.  The adjoint sweep and the
+ * immediate-mode gates always use FP64. */
+qf_status qf_program_set_fp64(qf_program *p, int exact);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
  * per shared-memory tile (default: the largest t with d^t amplitudes <= 8192

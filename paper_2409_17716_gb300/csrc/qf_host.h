@@ -22,6 +22,10 @@ struct StridedGeom {
     bool c_above = false;
 };
 StridedGeom uniform_geom(int d, int n, const TOp &op);
+// In-place conversion of a complex128 state between double2 and its
+// double-float form (k_df.cu): pack = double2 -> (hi.re, hi.im, lo.re, lo.im).
+cudaError_t launch_df_convert(cudaStream_t stream, int num_sms, void *psi, long long N, bool pack);
+
 template <typename R>
 cudaError_t launch_strided(const Launch &L, cplx<R> *psi, int d, int n, const TOp &op, const cplx<R> *mat, int nmat);
 template <typename R>
@@ -201,15 +205,17 @@ qf_status program_gates(const qf_program *p, std::vector<HGate> *out);
 
 // Tile passes of a program compiled at plan time (qf_jit.cu).
 struct JitProgram;
+// df: complex128 forward passes in double-float arithmetic (k_df.cu); their
+// prepared entries are 32 bytes, (urh, urh, -uih, uih, url, url, -uil, uil).
 qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                    int k_override, bool adj, int num_sms, JitProgram **out);
+                    int k_override, bool adj, int num_sms, JitProgram **out, bool df = false);
 qf_status jit_launch_adj(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, void *lam, double *rows,
                          const TileGeom &g, const void *prepared, int npool, const void *gpool);
 int jit_pass_grid(const JitProgram *jp, size_t pi);
 int jit_pass_ncols(const JitProgram *jp, size_t pi);
 void jit_free(JitProgram *jp);
 qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                     int k_override, bool adj, std::string *out);
+                     int k_override, bool adj, std::string *out, bool df = false);
 bool jit_pass_ready(const JitProgram *jp, size_t pi);
 bool jit_pass_global_pool(const JitProgram *jp, size_t pi);
 qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,

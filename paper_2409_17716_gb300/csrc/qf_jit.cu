@@ -133,10 +133,70 @@ __device__ __forceinline__ C jma(const P p, C a, C acc) {
     acc = __ffma2_rn(make_float2(p.x, p.y), a, acc);
     return __ffma2_rn(make_float2(p.z, p.w), make_float2(a.y, a.x), acc);
 }
-__device__ __forceinline__ C jrm(float m, C a) { return __fmul2_rn(make_float2(m, m), a); }
-__device__ __forceinline__ C jrma(float m, C a, C acc) { return __ffma2_rn(make_float2(m, m), a, acc); }
+__device__ __forceinline__ C jrm(const P p, C a) { return __fmul2_rn(make_float2(p.x, p.x), a); }
+__device__ __forceinline__ C jrma(const P p, C a, C acc) { return __ffma2_rn(make_float2(p.x, p.x), a, acc); }
+__device__ __forceinline__ C jn(C a) { return a; }
 #define QJ_CP_BYTES "8"
 #define QJ_CP_KIND "ca"
+#elif QJ_DF
+// Double-float complex128 (values hi + lo of two floats; C = (hi.re, hi.im,
+// lo.re, lo.im)).  An entry u = ur + i ui holds (urh, urh, -uih, uih) and
+// (url, url, -uil, uil), so one complex product is two paired products:
+// (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr).  Each paired product a * b of
+// hi/lo pairs is ph = ah * bh rounded plus pe = the exact error of ah * bh
+// (one FMA, Dekker's TwoProduct) + ah * bl + al * bh; sums keep their rounding
+// error exactly (Knuth's TwoSum) in the low part; jn renormalizes.
+typedef float4 C;
+struct __align__(16) P { float4 h, l; };
+__device__ __forceinline__ float2 qf2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 qng(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void qts(float2 a, float2 b, float2 &s, float2 &e) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, qng(a));
+    e = __fadd2_rn(__fadd2_rn(a, qng(__fadd2_rn(s, qng(bb)))), __fadd2_rn(b, qng(bb)));
+}
+__device__ __forceinline__ void qtp(float2 ah, float2 al, float2 bh, float2 bl, float2 &p, float2 &e) {
+    p = __fmul2_rn(ah, bh);
+    e = __ffma2_rn(ah, bh, qng(p));
+    e = __ffma2_rn(ah, bl, e);
+    e = __ffma2_rn(al, bh, e);
+}
+__device__ __forceinline__ C jm(const P p, C a) {
+    float2 p1, e1, p2, e2, s, t;
+    qtp(qf2(p.h.x, p.h.y), qf2(p.l.x, p.l.y), qf2(a.x, a.y), qf2(a.z, a.w), p1, e1);
+    qtp(qf2(p.h.z, p.h.w), qf2(p.l.z, p.l.w), qf2(a.y, a.x), qf2(a.w, a.z), p2, e2);
+    qts(p1, p2, s, t);
+    const float2 l = __fadd2_rn(__fadd2_rn(e1, e2), t);
+    return make_float4(s.x, s.y, l.x, l.y);
+}
+__device__ __forceinline__ C jma(const P p, C a, C acc) {
+    float2 p1, e1, p2, e2, s, t1, t2;
+    qtp(qf2(p.h.x, p.h.y), qf2(p.l.x, p.l.y), qf2(a.x, a.y), qf2(a.z, a.w), p1, e1);
+    qtp(qf2(p.h.z, p.h.w), qf2(p.l.z, p.l.w), qf2(a.y, a.x), qf2(a.w, a.z), p2, e2);
+    qts(qf2(acc.x, acc.y), p1, s, t1);
+    qts(s, p2, s, t2);
+    const float2 l = __fadd2_rn(__fadd2_rn(qf2(acc.z, acc.w), __fadd2_rn(e1, e2)), __fadd2_rn(t1, t2));
+    return make_float4(s.x, s.y, l.x, l.y);
+}
+__device__ __forceinline__ C jrm(const P p, C a) {
+    float2 q, e;
+    qtp(qf2(p.h.x, p.h.x), qf2(p.l.x, p.l.x), qf2(a.x, a.y), qf2(a.z, a.w), q, e);
+    return make_float4(q.x, q.y, e.x, e.y);
+}
+__device__ __forceinline__ C jrma(const P p, C a, C acc) {
+    float2 q, e, s, t;
+    qtp(qf2(p.h.x, p.h.x), qf2(p.l.x, p.l.x), qf2(a.x, a.y), qf2(a.z, a.w), q, e);
+    qts(qf2(acc.x, acc.y), q, s, t);
+    const float2 l = __fadd2_rn(qf2(acc.z, acc.w), __fadd2_rn(e, t));
+    return make_float4(s.x, s.y, l.x, l.y);
+}
+__device__ __forceinline__ C jn(C a) {
+    float2 s, t;
+    qts(qf2(a.x, a.y), qf2(a.z, a.w), s, t);
+    return make_float4(s.x, s.y, t.x, t.y);
+}
+#define QJ_CP_BYTES "16"
+#define QJ_CP_KIND "cg"
 #else
 typedef double2 C;
 typedef double2 P;
@@ -148,8 +208,9 @@ __device__ __forceinline__ C jma(const P p, C a, C acc) {
     acc.y = fma(p.x, a.y, acc.y); acc.y = fma(p.y, a.x, acc.y);
     return acc;
 }
-__device__ __forceinline__ C jrm(double m, C a) { return make_double2(m * a.x, m * a.y); }
-__device__ __forceinline__ C jrma(double m, C a, C acc) { return make_double2(fma(m, a.x, acc.x), fma(m, a.y, acc.y)); }
+__device__ __forceinline__ C jrm(const P p, C a) { return make_double2(p.x * a.x, p.x * a.y); }
+__device__ __forceinline__ C jrma(const P p, C a, C acc) { return make_double2(fma(p.x, a.x, acc.x), fma(p.x, a.y, acc.y)); }
+__device__ __forceinline__ C jn(C a) { return a; }
 #define QJ_CP_BYTES "16"
 #define QJ_CP_KIND "cg"
 #endif
@@ -188,6 +249,7 @@ int ipow_i(int d, int e) {
 struct PassSrc {
     int d, T, SEG, nt, kA, nruns, K, threads;
     bool c128, params;   // params: entries in the kernel parameters, else global
+    bool df = false;     // complex128 in double-float arithmetic (32-byte entries)
     int npool;
     bool adj = false;    // reverse pass of the adjoint sweep (psi and lambda, gradient columns)
     long long ntiles = 0;                        // tiles of the pass
@@ -235,6 +297,7 @@ class Gen {
         o_ << "  C *buf0 = reinterpret_cast<C *>(qj_sm + " << boff << ");\n";
         o_ << "  C *buf1 = buf0 + " << p_.slots() << ";   // tile of " << p_.T << " amplitudes\n";
         o_ << "  const int tid = threadIdx.x;\n";
+        emit_lanes();
         o_ << "  const bool db = A.mode != 0;\n";
         emit_offA(NA);
         o_ << "  __syncthreads();\n";
@@ -280,7 +343,12 @@ class Gen {
                 o_ << "if (" << c << " == 0 && sh) A.psi[g + 1] = dst[1]; else if (" << c << " == " << CH - 1
                    << " && !sh) A.psi[g] = dst[0]; else qj_st2(A.psi + g, dst); ";
         };
-        if (CH >= 64) {
+        if (lanes()) {
+            const int R = p_.threads / CH;
+            o_ << "    if (qj_tr < " << R << ") for (int a = qj_tr; a < " << NA << "; a += " << R << ") { ";
+            body("a", "qj_tu", "a * " + std::to_string(CH) + " + qj_tu");
+            o_ << "}\n";
+        } else if (CH >= 64) {
             o_ << "    for (int a = 0; a < " << NA << "; ++a) {\n      for (int c = tid; c < " << CH << "; c += "
                << p_.threads << ") { ";
             body("a", "c", "a * " + std::to_string(CH) + " + c");
@@ -336,6 +404,7 @@ class Gen {
         o_ << "  C *ltile = tile + " << p_.T << ";\n";
         o_ << "  long long *offA = reinterpret_cast<long long *>(qj_sm + " << (size_t)2 * p_.T * elt() << ");\n";
         o_ << "  const int tid = threadIdx.x;\n";
+        emit_lanes();
         for (int c = 0; c < NC; ++c) o_ << "  double g" << c << " = 0.0;\n";
         o_ << "  for (int a = tid; a < " << NA << "; a += " << p_.threads << ") {\n    long long o = 0; int rem = a;\n";
         for (int i = p_.kA - 1; i >= 0; --i)
@@ -389,7 +458,13 @@ class Gen {
             else if (pf == 2) o_ << "qj_st2(" << g << " + " << gi << ", " << sm << " + " << e << "); ";
             else o_ << g << "[" << gi << "] = " << sm << "[" << e << "]; ";
         };
-        if (per_run >= 64) {
+        if (lanes()) {
+            const int R = p_.threads / per_run;
+            o_ << "    if (qj_tr < " << R << ") for (int a = qj_tr; a < " << NA << "; a += " << R
+               << ") { const long long ro = base + offA[a]; const int l = qj_tu * " << pf << "; ";
+            for (auto &b : bufs) one(b.first, b.second, "a * " + std::to_string(p_.SEG) + " + l", "ro + l");
+            o_ << "}\n";
+        } else if (per_run >= 64) {
             o_ << "    for (int a = 0; a < " << NA << "; ++a) { const long long ro = base + offA[a];\n";
             o_ << "      for (int l = tid * " << pf << "; l < " << p_.SEG << "; l += " << p_.threads * pf << ") { ";
             for (auto &b : bufs) one(b.first, b.second, "a * " + std::to_string(p_.SEG) + " + l", "ro + l");
@@ -405,6 +480,25 @@ class Gen {
 
 
     size_t elt() const { return p_.c128 ? 16 : 8; }
+
+    // Copy units of one run: amplitude pairs (complex64, even d), padded
+    // pairs, or amplitudes.
+    int run_units() const {
+        if (p_.pad) return (p_.SEG + 1) / 2;
+        const int pf = (!p_.c128 && D_ % 2 == 0 && p_.SEG % 2 == 0) ? 2 : 1;
+        return p_.SEG / pf;
+    }
+
+    // At odd d, runs of at most 32 units move with a fixed lane layout:
+    // thread tid copies unit qj_tu of runs qj_tr, qj_tr + R, ... (R =
+    // threads / units), so no index is divided per element and a run's offset
+    // is read once (measured on GB300: d=5 passes 4 % faster; at even d the
+    // division is a shift and the layout lost 5 % at d=2).
+    bool lanes() const { return D_ % 2 == 1 && run_units() <= 32; }
+    void emit_lanes() {
+        const int U = run_units();
+        if (lanes()) o_ << "  const int qj_tr = tid / " << U << ", qj_tu = tid - qj_tr * " << U << ";\n";
+    }
 
   private:
     const PassSrc &p_;
@@ -584,11 +678,11 @@ class Gen {
         const std::string a = V(b0 + J * RS), c = V(b0 + L * RS);
         o_ << "      { const C qa = " << a << ", qc = " << c << ";\n";
         if (real) {
-            o_ << "        " << a << " = jrma(" << e1 << ".x, qc, jrm(" << e0 << ".x, qa));\n";
-            o_ << "        " << c << " = jrma(" << e3 << ".x, qc, jrm(" << e2 << ".x, qa)); }\n";
+            o_ << "        " << a << " = jn(jrma(" << e1 << ", qc, jrm(" << e0 << ", qa)));\n";
+            o_ << "        " << c << " = jn(jrma(" << e3 << ", qc, jrm(" << e2 << ", qa))); }\n";
         } else {
-            o_ << "        " << a << " = jma(" << e1 << ", qc, jm(" << e0 << ", qa));\n";
-            o_ << "        " << c << " = jma(" << e3 << ", qc, jm(" << e2 << ", qa)); }\n";
+            o_ << "        " << a << " = jn(jma(" << e1 << ", qc, jm(" << e0 << ", qa)));\n";
+            o_ << "        " << c << " = jn(jma(" << e3 << ", qc, jm(" << e2 << ", qa))); }\n";
         }
     }
 
@@ -618,7 +712,7 @@ class Gen {
                 for (int l = 0; l < D_; ++l) {
                     std::string acc = "jm(" + E(m + l * D_) + ", x0)";
                     for (int x = 1; x < D_; ++x) acc = "jma(" + E(m + l * D_ + x) + ", x" + std::to_string(x) + ", " + acc + ")";
-                    o_ << "        " << V(b0 + l * RS) << " = " << acc << ";\n";
+                    o_ << "        " << V(b0 + l * RS) << " = jn(" << acc << ");\n";
                 }
                 o_ << "      }\n";
             }
@@ -653,7 +747,7 @@ class Gen {
                 o_ << "      { const int dg = " << outside_digit(o.lsa) << "; if ((" << o.mask
                    << " >> dg) & 1) { const P ph = " << Edyn(std::to_string(m) + " + dg") << ";";
                 const int DK = ipow_i(D_, p_.K);
-                for (int r = 0; r < DK; ++r) o_ << " " << V(r) << " = jm(ph, " << V(r) << ");";
+                for (int r = 0; r < DK; ++r) o_ << " " << V(r) << " = jn(jm(ph, " << V(r) << "));";
                 o_ << " } }\n";
                 break;
             }
@@ -664,8 +758,8 @@ class Gen {
                 for (int b0 : fibres(sa))
                     for (int l = 0; l < D_; ++l)
                         if ((o.mask >> l) & 1)
-                            o_ << " " << V(b0 + l * RS) << " = jm(" << Edyn("mb + " + std::to_string(l)) << ", "
-                               << V(b0 + l * RS) << ");";
+                            o_ << " " << V(b0 + l * RS) << " = jn(jm(" << Edyn("mb + " + std::to_string(l)) << ", "
+                               << V(b0 + l * RS) << "));";
                 o_ << " } }\n";
                 break;
             }
@@ -678,7 +772,8 @@ class Gen {
                 }
                 o_ << "     ";
                 for (int l = 0; l < D_; ++l)
-                    if ((o.mask >> l) & 1) o_ << " " << V(b0 + l * RS) << " = jm(" << E(mb + l) << ", " << V(b0 + l * RS) << ");";
+                    if ((o.mask >> l) & 1)
+                        o_ << " " << V(b0 + l * RS) << " = jn(jm(" << E(mb + l) << ", " << V(b0 + l * RS) << "));";
                 o_ << "\n";
             }
             break;
@@ -740,7 +835,7 @@ class Gen {
         o_ << "      for (int r = 0; r < " << DK << "; ++r) xs[r] = " << tn_ << "[" << sx("(b + offs[r])") << "];\n";
         o_ << "      for (int r = 0; r < " << DK << "; ++r) { C acc = jm(A.gp[" << o.mat << " + r * " << DK
            << "], xs[0]); for (int x = 1; x < " << DK << "; ++x) acc = jma(A.gp[" << o.mat << " + r * " << DK
-           << " + x], xs[x], acc); " << tn_ << "[" << sx("(b + offs[r])") << "] = acc; }\n    }\n";
+           << " + x], xs[x], acc); " << tn_ << "[" << sx("(b + offs[r])") << "] = jn(acc); }\n    }\n";
     }
 };
 
@@ -787,7 +882,7 @@ struct JitProgram {
 // vector per pass; k_override > 0 sets the register slots per stage.
 static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops,
                                             int d, bool c128, int k_override, bool adj, JitProgram *jp,
-                                            std::vector<std::string> &names) {
+                                            std::vector<std::string> &names, bool df) {
     jp->passes.resize(plan.size());
     names.assign(plan.size(), std::string());
     std::vector<std::string> out(plan.size());
@@ -798,6 +893,7 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         PassSrc &ps = specs[pi];
         ps.d = d;
         ps.c128 = c128;
+        ps.df = df && c128 && !adj;
         ps.T = pp.geom.T;
         ps.SEG = pp.geom.SEG;
         ps.nt = pp.geom.nt;
@@ -836,7 +932,8 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
             }
         }
         ps.npool = npool;
-        ps.params = npool <= kParamPoolMax && !dense_k;
+        const int units = ps.df ? 2 : 1;   // 16-byte units per entry
+        ps.params = npool * units <= kParamPoolMax && !dense_k;
         const int DK = ipow_i(d, ps.K);
         // one register block per thread and stage where 128 threads cover
         // them; forward complex64 passes with up to 256 blocks also run 128
@@ -845,10 +942,10 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         const int nblk = ps.T / DK;
         ps.threads = (nblk <= 128 || (!adj && !c128 && nblk <= 256)) ? 128 : 256;
         std::ostringstream nm;
-        nm << (adj ? "k_tile_adj_jit_d" : "k_tile_jit_d") << d << (c128 ? "_c128_" : "_c64_") << pi;
+        nm << (adj ? "k_tile_adj_jit_d" : "k_tile_jit_d") << d << (ps.df ? "_c128df_" : c128 ? "_c128_" : "_c64_") << pi;
         names[pi] = nm.str();
         std::ostringstream src;
-        src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n" << kPrelude;
+        src << "#define QJ_C64 " << (c128 ? 0 : 1) << "\n#define QJ_DF " << (ps.df ? 1 : 0) << "\n" << kPrelude;
         Gen g(ps, src);
         g.tile_base_lit(names[pi]);
         if (adj) g.kernel_adj(names[pi]);
@@ -870,16 +967,16 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ji.npool = npool;
         ji.NG = std::max(1, 2 * ps.nruns + ps.kA);
         ji.pool_off = (ji.header + 8 * (size_t)ji.NG + 15) & ~(size_t)15;
-        ji.arg_bytes = ji.pool_off + 16 * (size_t)std::max(1, ps.params ? npool : 1);
+        ji.arg_bytes = ji.pool_off + 16 * (size_t)units * std::max(1, ps.params ? npool : 1);
     }
     return out;
 }
 
 qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                     int k_override, bool adj, std::string *out) {
+                     int k_override, bool adj, std::string *out, bool df) {
     JitProgram jp;
     std::vector<std::string> names;
-    std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, &jp, names);
+    std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, &jp, names, df);
     out->clear();
     for (const std::string &x : srcs)
         if (!x.empty()) *out += "// ---- translation unit\n" + x;
@@ -966,12 +1063,12 @@ bool nvrtc_compile(const std::string &code, const std::string &arch, std::vector
 // of this process first, then cubins cached on disk, then NVRTC (passes
 // compiled in parallel threads).
 qf_status jit_build(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
-                    int k_override, bool adj, int num_sms, JitProgram **out) {
+                    int k_override, bool adj, int num_sms, JitProgram **out, bool df) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!load_apis()) return set_error(QF_ERR_UNSUPPORTED, g_load_err);
     JitProgram *jp = new JitProgram();
     std::vector<std::string> names;
-    const std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, jp, names);
+    const std::vector<std::string> srcs = gen_sources(plan, ops, d, c128, k_override, adj, jp, names, df);
     int major = 10, minor = 3, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);

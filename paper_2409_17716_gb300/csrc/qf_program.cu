@@ -27,6 +27,8 @@ struct qf_program {
     int jit_k = 0;                     // register slots per compiled stage (0: default per d)
     JitProgram *jitp = nullptr;        // compiled passes of `plan` (nullptr: not built)
     bool jit_c128 = false;
+    bool jit_df = false;               // jitp holds double-float complex128 passes
+    bool fp64 = false;                 // complex128 compiled passes in FP64 (default: double-float)
     JitProgram *jitadj = nullptr;      // compiled reverse passes of `adj_plan`
     bool jitadj_c128 = false;
     int tile_qudits = 0, min_run_qudits = 0, max_ops = 0;   // planner overrides (0: default)
@@ -181,6 +183,19 @@ static void append_prepared(const ROp &r, std::vector<unsigned char> &out) {
     }
 }
 
+// Double-float entries of a resolved op for a complex128 pass in
+// double-float arithmetic: each FP64 entry split as hi = nearest float,
+// lo = nearest float to the remainder; 32 bytes (urh, urh, -uih, uih, url,
+// url, -uil, uil).
+static void append_prepared_df(const ROp &r, std::vector<unsigned char> &out) {
+    for (const cd &z : r.m) {
+        const float rh = (float)z.real(), ih = (float)z.imag();
+        const float rl = (float)(z.real() - (double)rh), il = (float)(z.imag() - (double)ih);
+        const float v[8] = {rh, rh, -ih, ih, rl, rl, -il, il};
+        out.insert(out.end(), (const unsigned char *)v, (const unsigned char *)v + 32);
+    }
+}
+
 static void drop_jit(qf_program *p) {
     if (p->jitp) {
         jit_free(p->jitp);
@@ -216,12 +231,14 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
     using C = cplx<R>;
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
-    if (!p->jitp || p->jit_c128 != c128) {
+    const bool df = c128 && !p->fp64;
+    if (!p->jitp || p->jit_c128 != c128 || p->jit_df != df) {
         drop_jit(p);
         std::vector<std::vector<TOp>> ops = jit_ops(p, params);
-        qf_status st = jit_build(p->plan, ops, d, c128, p->jit_k, false, s->num_sms, &p->jitp);
+        qf_status st = jit_build(p->plan, ops, d, c128, p->jit_k, false, s->num_sms, &p->jitp, df);
         if (st != QF_OK) return st;
         p->jit_c128 = c128;
+        p->jit_df = df;
     }
     // entries of every pass at these parameters; passes reading them from
     // global memory get a copy in the program's upload buffer
@@ -236,7 +253,11 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
             single[pi] = resolve_group(p->gates, pp.groups[0], d, params);
             continue;
         }
-        for (const auto &grp : pp.groups) append_prepared<R>(resolve_group(p->gates, grp, d, params), prep[pi]);
+        for (const auto &grp : pp.groups) {
+            const ROp r = resolve_group(p->gates, grp, d, params);
+            if (df) append_prepared_df(r, prep[pi]);
+            else append_prepared<R>(r, prep[pi]);
+        }
         if (jit_pass_global_pool(p->jitp, pi)) {
             goff[pi] = align16(host.size());
             host.resize(goff[pi] + prep[pi].size());
@@ -262,6 +283,15 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
         QF_CUDA(cudaEventRecord(p->tev[prev_ev], s->stream));
     }
     const long long N = ipow_ll(d, n);
+    // double-float passes work on the state converted in place; strided and
+    // multi-controlled passes (FP64 kernels) and the caller see double2
+    bool packed = false;
+    auto convert = [&](bool pack) -> qf_status {
+        cudaError_t e = launch_df_convert(s->stream, s->num_sms, s->data, N, pack);
+        if (e != cudaSuccess) return cuda_error(e, "double-float conversion");
+        packed = pack;
+        return QF_OK;
+    };
     for (size_t pi = 0; pi < np; ++pi) {
         const PassPlan &pp = p->plan[pi];
         if (pp.strided || pp.mc) {
@@ -269,6 +299,10 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
             if ((o.kind == OP_SHIFT && o.s == 0) || (o.kind == OP_DIAG && o.mask == 0) ||
                 (o.kind == OP_MCSHIFT && o.s == 0))
                 continue;
+            if (packed) {
+                qf_status cst = convert(false);
+                if (cst != QF_OK) return cst;
+            }
             std::vector<C> m(single[pi].m.size());
             for (size_t i = 0; i < m.size(); ++i) m[i] = mk<R>((R)single[pi].m[i].real(), (R)single[pi].m[i].imag());
             if (p->timing) {
@@ -279,6 +313,10 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
                                   : launch_strided<R>(L, psi, d, n, o, m.data(), (int)m.size());
             if (e != cudaSuccess) return cuda_error(e, "program pass");
         } else {
+            if (df && !packed) {
+                qf_status cst = convert(true);
+                if (cst != QF_OK) return cst;
+            }
             if (p->timing) {
                 p->tkind.push_back(0);
                 p->tbytes.push_back(2.0 * sizeof(C) * (double)N);
@@ -298,6 +336,10 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
             p->tafter.push_back(cur);
             prev_ev = cur;
         }
+    }
+    if (packed) {
+        qf_status cst = convert(false);
+        if (cst != QF_OK) return cst;
     }
     QF_CUDA(cudaEventRecord(p->done_ev, s->stream));
     p->ran = true;
@@ -1126,7 +1168,7 @@ qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, int adjoint, char *b
             drop_jit(p);
         }
         std::vector<std::vector<TOp>> ops = jit_ops(p, zeros.data());
-        st = jit_source(p->plan, ops, p->d, c128, p->jit_k, false, &src);
+        st = jit_source(p->plan, ops, p->d, c128, p->jit_k, false, &src, c128 && !p->fp64);
     }
     if (st != QF_OK) return st;
     if (len) *len = src.size() + 1;
@@ -1150,6 +1192,15 @@ qf_status qf_program_set_stage_slots(qf_program *p, int slots) {
     if (slots < 0 || slots > kMaxStageK) return set_error(QF_ERR_ARG, "stage slots must be in [0, 6]");
     p->jit_k = slots;
     drop_jit(p);
+    return QF_OK;
+}
+
+qf_status qf_program_set_fp64(qf_program *p, int exact) {
+    if (!p) return set_error(QF_ERR_ARG, "program is NULL");
+    if (p->fp64 != (exact != 0)) {
+        p->fp64 = exact != 0;
+        if (p->jit_c128) drop_jit(p);
+    }
     return QF_OK;
 }
 

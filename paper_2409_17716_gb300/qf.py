@@ -83,6 +83,7 @@ _PROTOS = {
     "qf_program_add_mcx": (_int, [_vp, _c.POINTER(_int), _int, _int, _int]),
     "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
+    "qf_program_set_fp64": (_int, [_vp, _int]),
     "qf_program_set_jit": (_int, [_vp, _int]),
     "qf_program_set_stage_slots": (_int, [_vp, _int]),
     "qf_program_jit_source": (_int, [_vp, _int, _int, _c.c_char_p, _c.c_size_t, _c.POINTER(_c.c_size_t)]),
@@ -462,6 +463,12 @@ def qf_program_jit_source(p: int, dtype: int = QF_C64, adjoint: bool = False) ->
 
 def qf_program_set_fusion(p: int, enable: bool) -> None:
     _call("qf_program_set_fusion", p, 1 if enable else 0)
+
+
+def qf_program_set_fp64(p: int, exact: bool) -> None:
+    """Complex128 compiled passes in FP64 (exact=True) or double-float
+    arithmetic (exact=False, the default)."""
+    _call("qf_program_set_fp64", p, 1 if exact else 0)
 
 
 def qf_program_run(p: int, s: int, params=None) -> None:
