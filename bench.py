@@ -424,7 +424,10 @@ def main():
     if extras:
         line["per_size"] = per_size_throughput(qf, W, torch, sizes, states, progs, args)
         line["unfused"] = unfused_throughput(qf, W, torch, sizes, states, circ)
-        line["c128"] = c128_throughput(qf, W, torch, sizes)
+        rates = qf.qf_device_fma_rates()
+        line["alu_peaks"] = {"fp64_fma_tflops": 2 * rates[0] / 1e12, "fp32_fma_tflops": 2 * rates[1] / 1e12,
+                             "how": "qf_device_fma_rates: independent FMA chains, CUDA events, best of 5"}
+        line["c128"] = c128_throughput(qf, W, torch, sizes, hbm_peak, rates)
         line["per_gate"] = per_gate_sweep(qf, W, torch, hbm_peak)
         line["e2e"] = e2e_throughput(qf, W, torch, sizes, progs, args)
     for p in progs:
@@ -507,19 +510,38 @@ def unfused_throughput(qf, W, torch, sizes, states, circ):
     return {"value": tot_au / (tot_ms / 1e3), "unit": UNIT, "note": "one kernel per gate (fusion off)"}
 
 
-def c128_throughput(qf, W, torch, sizes):
+def c128_throughput(qf, W, torch, sizes, hbm_peak, rates):
+    """Complex128 programs (double-float arithmetic in the compiled passes,
+    the default) per size, with the two ceilings that bound them: HBM (one
+    read and write of 16-byte amplitudes per pass) and what FP64 arithmetic
+    alone would allow (4 FP64 FMAs per complex multiply-add of the program,
+    at the measured FP64 FMA rate); the same programs in FP64 on the
+    smallest size for comparison."""
+    fp64_rate = rates[0]
     tot_au, tot_ms, per = 0, 0.0, []
     for d, n in sizes:
         st = qf.State(d, n, "c128").set_basis(0)
         p = qf.program_from_ops(d, n, W.random_circuit(d, n, N_GATES), fuse=True)
         qf.qf_program_run(p, st.handle)
         ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=3)
-        per.append({"d": d, "n": n, "ms": ms, "passes": qf.qf_program_last_passes(p)})
+        passes = qf.qf_program_last_passes(p)
+        N = d ** n
+        cm = qf.qf_program_cmacs(p, qf.QF_C128)
+        rec = {"d": d, "n": n, "ms": ms, "passes": passes, "au_per_s": N * N_GATES / (ms / 1e3),
+               "cmacs_per_amplitude": cm,
+               "hbm_bound_au_per_s": N * N_GATES / (passes * 2 * 16 * N / (hbm_peak * 1e9)),
+               "fp64_arith_bound_au_per_s": fp64_rate * N_GATES / (4 * cm) if cm else None}
+        if (d, n) == (3, 17):
+            qf.qf_program_set_fp64(p, True)
+            qf.qf_program_run(p, st.handle)
+            rec["fp64_ms"] = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=2)
+        per.append(rec)
         qf.qf_program_free(p)
         st.free()
-        tot_au += d ** n * N_GATES
+        tot_au += N * N_GATES
         tot_ms += ms
-    return {"value": tot_au / (tot_ms / 1e3), "unit": UNIT, "per_size": per}
+    return {"value": tot_au / (tot_ms / 1e3), "unit": UNIT, "arith": "double-float (FP32 pairs) in compiled passes",
+            "bound": "alu (FP32 pipe, double-float arithmetic)", "per_size": per}
 
 
 def per_gate_sweep(qf, W, torch, hbm_peak):

@@ -302,6 +302,20 @@ qf_status qf_program_set_fusion(qf_program *p, int enable);
  * 2^-96 and smaller ones become 0.  The adjoint sweep and the
  * immediate-mode gates always use FP64. */
 qf_status qf_program_set_fp64(qf_program *p, int exact);
+/* Arithmetic of the program as planned for dtype dt: complex multiply-adds
+ * per amplitude summed over its fused ops (a multiply-add with a real entry
+ * counts one half; permutations count zero).  Host only; no counterpart in
+ * the paper (a measurement aid: with the device rates below it gives the
+ * rate the arithmetic units alone would allow).  QF_ERR_UNSUPPORTED for
+ * programs on mixed-dimension registers. */
+qf_status qf_program_cmacs(qf_program *p, qf_dtype dt, double *cmacs_per_amplitude);
+/* FP64 and FP32 fused multiply-add throughput of the current device (FMA/s),
+ * measured on cuda_stream (synchronised) with eight independent FMA chains
+ * per thread on 8 CTAs of 256 threads per SM, best of five timed launches
+ * (CUDA events), at the clocks the GPU runs.  No counterpart in the paper:
+ * it states which arithmetic unit bounds a pass.  Allocates and frees a
+ * small device buffer; QF_ERR_OOM if that fails. */
+qf_status qf_device_fma_rates(void *cuda_stream, double *fp64_fma_per_s, double *fp32_fma_per_s);
 
 /* Tiling of fused passes (0 = default for each): tile_qudits = local qudits
  * per shared-memory tile (default: the largest t with d^t amplitudes <= 8192

@@ -1258,6 +1258,48 @@ qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_
     return QF_OK;
 }
 
+// Complex multiply-adds per amplitude of one resolved op (a real entry
+// counts half): what the arithmetic units execute, independent of HBM.
+static double op_cmacs(const TOp &o, int d) {
+    const double ctrl = (double)(d - 1) / d;   // control level 0 is the identity
+    int pc = 0;
+    for (int m = o.mask; m; m &= m - 1) ++pc;
+    switch (o.kind) {
+    case OP_DENSE: return d;
+    case OP_PAIR: return (o.s == 1 ? 2.0 : 4.0) / d;
+    case OP_DIAG: return (double)pc / d;
+    case OP_CPAIR: return ctrl * (o.s == 1 ? 2.0 : 4.0) / d;
+    case OP_CDIAG: return ctrl * (double)pc / d;
+    case OP_DENSEK: {
+        double k = 1;
+        for (int i = 0; i < o.nq; ++i) k *= d;
+        return k;
+    }
+    default: return 0.0;   // permutations (shift, SUM, SWAP, multi-controlled shift)
+    }
+}
+
+qf_status qf_program_cmacs(qf_program *p, qf_dtype dt, double *cmacs_per_amplitude) {
+    if (!p || !cmacs_per_amplitude) return set_error(QF_ERR_ARG, "program or output is NULL");
+    if (p->mixed) return set_error(QF_ERR_UNSUPPORTED, "qf_program_cmacs: mixed-dimension programs");
+    qf_status st = qf_program_plan(p, dt, nullptr, nullptr, nullptr);
+    if (st != QF_OK) return st;
+    std::vector<double> zeros((size_t)std::max(p->num_params, 1), 0.0);
+    double total = 0.0;
+    for (const PassPlan &pp : p->plan)
+        for (const auto &grp : pp.groups) {
+            const ROp r = resolve_group(p->gates, grp, p->d, zeros.data());
+            if (r.op.kind == OP_MCDENSE) {
+                // changes the fibres whose controls sit at their levels
+                total += p->d / std::pow((double)p->d, (double)r.op.nq);
+            } else {
+                total += op_cmacs(r.op, p->d);
+            }
+        }
+    *cmacs_per_amplitude = total;
+    return QF_OK;
+}
+
 qf_status qf_program_stages(qf_program *p, qf_dtype dt, int *num_tile_passes, int *num_stages, int *num_ops) {
     if (!p) return set_error(QF_ERR_ARG, "program is NULL");
     if (p->mixed) {

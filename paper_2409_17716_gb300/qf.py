@@ -84,6 +84,8 @@ _PROTOS = {
     "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
     "qf_program_set_fp64": (_int, [_vp, _int]),
+    "qf_program_cmacs": (_int, [_vp, _int, _c.POINTER(_dbl)]),
+    "qf_device_fma_rates": (_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_dbl)]),
     "qf_program_set_jit": (_int, [_vp, _int]),
     "qf_program_set_stage_slots": (_int, [_vp, _int]),
     "qf_program_jit_source": (_int, [_vp, _int, _int, _c.c_char_p, _c.c_size_t, _c.POINTER(_c.c_size_t)]),
@@ -463,6 +465,20 @@ def qf_program_jit_source(p: int, dtype: int = QF_C64, adjoint: bool = False) ->
 
 def qf_program_set_fusion(p: int, enable: bool) -> None:
     _call("qf_program_set_fusion", p, 1 if enable else 0)
+
+
+def qf_program_cmacs(p: int, dtype: int = QF_C64) -> float:
+    """Complex multiply-adds per amplitude of the planned program."""
+    out = _dbl()
+    _call("qf_program_cmacs", p, dtype, _c.byref(out))
+    return out.value
+
+
+def qf_device_fma_rates(stream=None):
+    """(FP64 FMA/s, FP32 FMA/s) of the current device."""
+    a, b = _dbl(), _dbl()
+    _call("qf_device_fma_rates", _stream_ptr(stream), _c.byref(a), _c.byref(b))
+    return a.value, b.value
 
 
 def qf_program_set_fp64(p: int, exact: bool) -> None:
