@@ -127,6 +127,26 @@ qf_status qf_state_set_basis(qf_state *s, long long index);
 /* dst <- src (same d, n, dtype); both on dst's stream. */
 qf_status qf_state_copy(qf_state *dst, const qf_state *src);
 
+/* Host buffers <-> amplitudes [first, first + count) of the state (the
+ * State class of "Library Architecture" holds the amplitude vector; these
+ * move it between host and device).  `host` holds count amplitudes in the
+ * state's layout (interleaved re, im; float for QF_C64, double for
+ * QF_C128).  One cudaMemcpyAsync on the state's stream: asynchronous for
+ * page-locked host memory (the buffer must stay valid and, for upload,
+ * unchanged until the stream reaches the copy), synchronous for pageable
+ * memory.  QF_ERR_ARG for a NULL buffer or a range outside the state. */
+qf_status qf_state_upload(qf_state *s, const void *host, long long first, long long count);
+qf_status qf_state_download(qf_state *s, void *host, long long first, long long count);
+
+/* Page-locked host memory for the copies above (no counterpart in the
+ * paper): `bytes` rounded up to 2 MiB of anonymous pages, registered with
+ * the CUDA driver; *out receives the address.  On GB300 with a Grace host,
+ * uploads from this memory ran without the 150-400 ms stalls measured for
+ * cudaHostAlloc memory.  Free with qf_host_free (QF_ERR_ARG for any other
+ * pointer).  QF_ERR_OOM if mapping or page-locking fails. */
+qf_status qf_host_alloc(size_t bytes, void **out);
+qf_status qf_host_free(void *p);
+
 /* ---------------------------------------------------------------- gates */
 
 /* Custom gate (section "Quantum Gates": users may supply a matrix; the

@@ -6,6 +6,11 @@
 #include <cstring>
 #include <string>
 
+#include <sys/mman.h>
+
+#include <map>
+#include <mutex>
+
 #include "qf_host.h"
 
 namespace qf {
@@ -365,6 +370,75 @@ qf_status qf_state_copy(qf_state *dst, const qf_state *src) {
     const size_t bytes = (size_t)dst->N * (dst->dt == QF_C64 ? 8 : 16);
     QF_CUDA(cudaMemcpyAsync(dst->data, src->data, bytes, cudaMemcpyDeviceToDevice, dst->stream));
     return QF_OK;
+}
+
+// Page-locked host memory: anonymous pages of the process, mapped here and
+// registered with the driver.  Measured on GB300 (Grace host): 7.3 GB of
+// uploads per step from such pages never stalled in 42 steps, while the same
+// copies from cudaHostAlloc memory stalled for 150-400 ms in 3 to 6 of 14
+// steps, copies alone included.
+static std::mutex g_host_mu;
+static std::map<void *, size_t> g_host_maps;
+
+qf_status qf_host_alloc(size_t bytes, void **out) {
+    if (!out) return set_error(QF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (bytes == 0) return set_error(QF_ERR_ARG, "qf_host_alloc: zero bytes");
+    const size_t huge = (size_t)2 << 20;
+    const size_t len = (bytes + huge - 1) / huge * huge;
+    void *p = mmap(nullptr, len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (p == MAP_FAILED) return set_error(QF_ERR_OOM, "qf_host_alloc: mmap of " + std::to_string(len) + " bytes failed");
+    madvise(p, len, MADV_HUGEPAGE);   // a hint; ignored where transparent huge pages are off
+    const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+    if (e != cudaSuccess) {
+        munmap(p, len);
+        cudaGetLastError();
+        return set_error(QF_ERR_OOM, std::string("qf_host_alloc: page-locking failed: ") + cudaGetErrorString(e));
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        g_host_maps[p] = len;
+    }
+    *out = p;
+    return QF_OK;
+}
+
+qf_status qf_host_free(void *p) {
+    if (!p) return QF_OK;
+    size_t len = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        auto it = g_host_maps.find(p);
+        if (it == g_host_maps.end()) return set_error(QF_ERR_ARG, "qf_host_free: pointer not from qf_host_alloc");
+        len = it->second;
+        g_host_maps.erase(it);
+    }
+    cudaHostUnregister(p);
+    munmap(p, len);
+    return QF_OK;
+}
+
+// Host <-> state copies of amplitudes [first, first + count): one
+// cudaMemcpyAsync over the contiguous range, on the state's stream.
+static qf_status host_copy(qf_state *s, void *host, long long first, long long count, bool up) {
+    if (!s) return set_error(QF_ERR_ARG, "state handle is NULL");
+    if (!host) return set_error(QF_ERR_ARG, "host buffer is NULL");
+    if (first < 0 || count < 0 || first > s->N || count > s->N - first)
+        return set_error(QF_ERR_ARG, "amplitude range outside the state");
+    if (count == 0) return QF_OK;
+    const size_t b = s->dt == QF_C64 ? 8 : 16;
+    char *dev = (char *)s->data + (size_t)first * b;
+    if (up) QF_CUDA(cudaMemcpyAsync(dev, host, (size_t)count * b, cudaMemcpyHostToDevice, s->stream));
+    else QF_CUDA(cudaMemcpyAsync(host, dev, (size_t)count * b, cudaMemcpyDeviceToHost, s->stream));
+    return QF_OK;
+}
+
+qf_status qf_state_upload(qf_state *s, const void *host, long long first, long long count) {
+    return host_copy(s, const_cast<void *>(host), first, count, true);
+}
+
+qf_status qf_state_download(qf_state *s, void *host, long long first, long long count) {
+    return host_copy(s, host, first, count, false);
 }
 
 static HGate one(int kind, int q) {

@@ -84,6 +84,10 @@ _PROTOS = {
     "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
     "qf_program_set_fp64": (_int, [_vp, _int]),
+    "qf_state_upload": (_int, [_vp, _vp, _c.c_longlong, _c.c_longlong]),
+    "qf_host_alloc": (_int, [_c.c_size_t, _c.POINTER(_vp)]),
+    "qf_host_free": (_int, [_vp]),
+    "qf_state_download": (_int, [_vp, _vp, _c.c_longlong, _c.c_longlong]),
     "qf_program_cmacs": (_int, [_vp, _int, _c.POINTER(_dbl)]),
     "qf_device_fma_rates": (_int, [_vp, _c.POINTER(_dbl), _c.POINTER(_dbl)]),
     "qf_program_set_jit": (_int, [_vp, _int]),
@@ -465,6 +469,35 @@ def qf_program_jit_source(p: int, dtype: int = QF_C64, adjoint: bool = False) ->
 
 def qf_program_set_fusion(p: int, enable: bool) -> None:
     _call("qf_program_set_fusion", p, 1 if enable else 0)
+
+
+def qf_host_alloc(nbytes: int) -> int:
+    """Page-locked host memory from the library (free with qf_host_free)."""
+    h = _vp()
+    _call("qf_host_alloc", int(nbytes), _c.byref(h))
+    return h.value
+
+
+def qf_host_free(ptr: int) -> None:
+    _call("qf_host_free", ptr)
+
+
+def host_array(ptr: int, count: int, dtype) -> np.ndarray:
+    """A numpy view of `count` elements of `dtype` at host address ptr (memory
+    from qf_host_alloc; the view must not outlive qf_host_free)."""
+    dt = np.dtype(dtype)
+    buf = (_c.c_char * (count * dt.itemsize)).from_address(ptr)
+    return np.frombuffer(buf, dtype=dt, count=count)
+
+
+def qf_state_upload(s: int, host_ptr: int, first: int, count: int) -> None:
+    """Amplitudes [first, first + count) of the state from host memory at host_ptr."""
+    _call("qf_state_upload", s, host_ptr, first, count)
+
+
+def qf_state_download(s: int, host_ptr: int, first: int, count: int) -> None:
+    """Amplitudes [first, first + count) of the state to host memory at host_ptr."""
+    _call("qf_state_download", s, host_ptr, first, count)
 
 
 def qf_program_cmacs(p: int, dtype: int = QF_C64) -> float:
