@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip c128/unfused/sweep/e2e/cpu legs")
     ap.add_argument("--profile-case", nargs="?", const="3,17", default=None, metavar="D,N",
                     help="small run for ncu captures: one state (default d=3 n=17) complex64 only, no extras")
+    ap.add_argument("--probe-host-memory", action="store_true",
+                    help="time the end-to-end step with host buffers from torch pin_memory and from qf_host_alloc "
+                         "(copies alone and with circuits) and print the per-step times; no bench line")
     args = ap.parse_args()
     if args.profile_case is not None:
         d, n = (int(x) for x in args.profile_case.split(","))
@@ -324,6 +327,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.probe_host_memory:
+        return probe_host_memory(args)
 
     import numpy as np
     import torch
@@ -933,6 +938,64 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
             "value_at_median_step": au / steps / (med / 1e3),
             "note": "per state (own stream, smallest first): qf_state_upload from page-locked host memory "
                     "(qf_host_alloc), qf_program_run, qf_expect to the host"}
+
+
+def probe_host_memory(args):
+    """The end-to-end step (per state and stream: qf_state_upload of 1.0-2.1
+    GB, the circuit, qf_expect) with host buffers from torch's pin_memory
+    and from the library's qf_host_alloc; per-step wall times."""
+    import numpy as np
+    import torch
+    from paper_2409_17716_gb300 import build as gpu_build
+    gpu_build.build()
+    from paper_2409_17716_gb300 import qf
+    from paper_2409_17716_gb300 import workloads as W
+    sizes = SIZES
+    progs = [qf.program_from_ops(d, n, W.random_circuit(d, n, N_GATES)) for d, n in sizes]
+    streams = [torch.cuda.Stream() for _ in sizes]
+    states = [qf.State(d, n, "c64", stream=s) for (d, n), s in zip(sizes, streams)]
+
+    def run(name, ptrs, circuits=True, steps=14):
+        per = []
+        for it in range(steps + 2):
+            t0 = time.perf_counter()
+            for i, st in enumerate(states):
+                qf.qf_state_upload(st.handle, ptrs[i], 0, sizes[i][0] ** sizes[i][1])
+                if circuits:
+                    qf.qf_program_run(progs[i], st.handle)
+            if circuits:
+                for st in states:
+                    qf.qf_expect(st.handle, qf.QF_OBS_NUMBER_ALL)
+            else:
+                for s in streams:
+                    s.synchronize()
+            if it >= 2:
+                per.append(round(1e3 * (time.perf_counter() - t0), 1))
+        med = sorted(per)[len(per) // 2]
+        print(json.dumps({"host_memory": name, "median_ms": med, "max_ms": max(per),
+                          "steps_over_1.5x_median": sum(p > 1.5 * med for p in per), "step_ms": per}), flush=True)
+
+    pinned = []
+    for d, n in sizes:
+        h = torch.zeros(d ** n, dtype=torch.complex64, pin_memory=True)
+        h[0] = 1.0
+        pinned.append(h)
+    tp = [h.data_ptr() for h in pinned]
+    run("torch pin_memory, uploads only", tp, circuits=False)
+    run("torch pin_memory, upload + circuit + <N_q>", tp)
+    del pinned
+    lib = []
+    for d, n in sizes:
+        ptr = qf.qf_host_alloc(d ** n * 8)
+        a = qf.host_array(ptr, d ** n, np.complex64)
+        a[:] = 0
+        a[0] = 1.0
+        lib.append(ptr)
+    run("qf_host_alloc, uploads only", lib, circuits=False)
+    run("qf_host_alloc, upload + circuit + <N_q>", lib)
+    for ptr in lib:
+        qf.qf_host_free(ptr)
+    return 0
 
 
 if __name__ == "__main__":
