@@ -367,9 +367,10 @@ def main():
     out_dev = torch.zeros(128, dtype=torch.float64, device="cuda")
 
     def step(states_, progs_):
+        # the program, then <N_q> of every qudit and the norm, reduced in its
+        # last pass
         for st, p in zip(states_, progs_):
-            qf.qf_program_run(p, st.handle)
-            qf.qf_expect_device(st.handle, out_dev.data_ptr(), qf.QF_OBS_NUMBER_ALL)
+            qf.qf_program_run_expect(p, st.handle, out_dev.data_ptr())
 
     for _ in range(args.warmup):
         step(states, progs)
@@ -405,7 +406,7 @@ def main():
                 strided_bytes += b_
     au_step = sum(d ** n for d, n in sizes) * N_GATES
     ms, value = whole_job(ms, au_step, args.steps, dist, "cuda")
-    launches = sum(pp + 2 for pp in passes) * args.steps
+    launches = sum(pp + 1 for pp in passes) * args.steps   # passes + the row sums of the fused reduction
     achieved = (tile_bytes / (tile_ms / 1e3)) / 1e9 if tile_ms > 0 else None
     ratio = traffic_ratio()
     avg_alg = tile_bytes / n_tile if n_tile else None

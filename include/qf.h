@@ -322,6 +322,17 @@ qf_status qf_program_set_fusion(qf_program *p, int enable);
  * 2^-96 and smaller ones become 0.  The adjoint sweep and the
  * immediate-mode gates always use FP64. */
 qf_status qf_program_set_fp64(qf_program *p, int exact);
+/* qf_program_run followed by <N_q> of every qudit and the norm ("Code
+ * style": measure returns the marginals; <N_q> = sum_m m P_q(m)) into out_dev
+ * (device, n + 1 FP64 values, 8-byte aligned), asynchronously on the state's
+ * stream: what qf_program_run and qf_expect_device with QF_OBS_NUMBER_ALL
+ * compute, in one pass fewer where the program's last pass is a compiled
+ * complex64 tile pass -- it sums |psi|^2 weighted by every qudit's level
+ * while its final tile is in shared memory (FP32 within a tile, FP64 across
+ * tiles, the same order on every run).  Otherwise the separate reduction
+ * runs after the program.  Errors as qf_program_run; QF_ERR_ARG for a NULL or
+ * misaligned out_dev. */
+qf_status qf_program_run_expect(qf_program *p, qf_state *s, const double *params, double *out_dev);
 /* Arithmetic of the program as planned for dtype dt: complex multiply-adds
  * per amplitude summed over its fused ops (a multiply-add with a real entry
  * counts one half; permutations count zero).  Host only; no counterpart in

@@ -180,13 +180,24 @@ __global__ void __launch_bounds__(256) k_expect_number_generic(const cplx<R> *__
     }
 }
 
-// Sums `rows` rows of `cols` partials in row order.
+// Sums `rows` rows of `cols` partials: one warp per column, lane l adding
+// rows l, l + 32, ... in order, then a fixed shuffle tree, so the result is
+// the same on every run (launched with 32 threads per column, at most 1024).
 __global__ void k_sum_partials(const double *partials, int rows, int cols, double *out) {
-    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = threadIdx.x >> 5; c < cols; c += nw) {
         double s = 0.0;
-        for (int r = 0; r < rows; ++r) s += partials[(long long)r * cols + c];
-        out[c] = s;
+        for (int r = lane; r < rows; r += 32) s += partials[(long long)r * cols + c];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[c] = s;
     }
+}
+
+static unsigned sum_threads(int cols) { return 32u * (unsigned)(cols < 1 ? 1 : cols > 32 ? 32 : cols); }
+
+cudaError_t launch_sum_rows(cudaStream_t stream, const double *rows, int nrows, int cols, double *out) {
+    k_sum_partials<<<1, sum_threads(cols), 0, stream>>>(rows, nrows, cols, out);
+    return cudaGetLastError();
 }
 
 // Fibre reduction over target qudit q (stride S): kind 0 = marginal P_q(m)
@@ -270,7 +281,7 @@ cudaError_t launch_expect_number(const Launch &L, const cplx<R> *psi, int d, int
         blocks = (int)(b < maxb ? b : maxb);
         k_expect_number_generic<R><<<blocks, 256, 0, L.stream>>>(psi, d, n, N, partials);
     }
-    k_sum_partials<<<1, 64, 0, L.stream>>>(partials, blocks, n + 1, out_dev);
+    k_sum_partials<<<1, sum_threads(n + 1), 0, L.stream>>>(partials, blocks, n + 1, out_dev);
     return cudaGetLastError();
 }
 
@@ -299,7 +310,7 @@ cudaError_t launch_fibre_reduce_g(const Launch &L, const cplx<R> *psi, int d, lo
     long long b = (nfib + 255) / 256;
     int blocks = (int)(b < maxb ? b : maxb);
     k_fibre_reduce<R><<<blocks, 256, 0, L.stream>>>(psi, d, nfib, S, kind, obs_dev, partials);
-    k_sum_partials<<<1, 32, 0, L.stream>>>(partials, blocks, kind == 0 ? d : 2, out_dev);
+    k_sum_partials<<<1, sum_threads(kind == 0 ? d : 2), 0, L.stream>>>(partials, blocks, kind == 0 ? d : 2, out_dev);
     return cudaGetLastError();
 }
 
@@ -376,7 +387,7 @@ static cudaError_t noalloc_launch(cudaStream_t stream, int sms, const cplx<R> *p
         blocks = (int)(b < maxb ? b : maxb);
         k_expect_number_generic<R><<<blocks, 256, 0, stream>>>(psi, d, n, N, partials);
     }
-    k_sum_partials<<<1, 64, 0, stream>>>(partials, blocks, n + 1, out_dev);
+    k_sum_partials<<<1, sum_threads(n + 1), 0, stream>>>(partials, blocks, n + 1, out_dev);
     return cudaGetLastError();
 }
 
@@ -524,7 +535,7 @@ cudaError_t launch_marginal_dims(const Launch &L, const cplx<R> *psi, const int 
         if (e != cudaSuccess) return e;
     }
     k_marginal<R><<<blocks, 256, smem, L.stream>>>(psi, N, M, partials);
-    k_sum_partials<<<1, 256, 0, L.stream>>>(partials, blocks, M.bins, out_dev);
+    k_sum_partials<<<1, sum_threads(M.bins), 0, L.stream>>>(partials, blocks, M.bins, out_dev);
     return cudaGetLastError();
 }
 

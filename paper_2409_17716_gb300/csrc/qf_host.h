@@ -217,9 +217,14 @@ void jit_free(JitProgram *jp);
 qf_status jit_source(const std::vector<PassPlan> &plan, std::vector<std::vector<TOp>> &ops, int d, bool c128,
                      int k_override, bool adj, std::string *out, bool df = false);
 bool jit_pass_ready(const JitProgram *jp, size_t pi);
+// Whether pass pi reduces <N_q> into per-CTA rows (jit_launch's rows, n + 1
+// doubles per CTA of jit_pass_grid) when given them.
+bool jit_pass_reduces(const JitProgram *jp, size_t pi);
+// out[c] = sum over `rows` rows of rows[r * cols + c] (k_reduce.cu).
+cudaError_t launch_sum_rows(cudaStream_t stream, const double *rows, int nrows, int cols, double *out);
 bool jit_pass_global_pool(const JitProgram *jp, size_t pi);
 qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,
-                     const void *prepared, int npool, const void *gpool);
+                     const void *prepared, int npool, const void *gpool, double *rows = nullptr);
 
 // Immediate application of one resolved op on a mixed-dimension state.
 qf_status run_op_mixed(qf_state *s, const ROp &r);

@@ -265,6 +265,14 @@ struct PassSrc {
     // plus the tile base is odd (every stride is odd).
     bool pad = false;
     int slots() const { return pad ? (T / SEG) * (SEG + 1) : T; }   // amplitudes of one tile buffer
+    // <N_q> and the norm reduced in this pass (the last pass of a complex64
+    // program, when the caller asks for them): global qudit of each local
+    // position, and for each outer qudit x the divisor D_x of the tile index
+    // (digit = (t / D_x) mod d)
+    bool red = false;
+    int n = 0;
+    std::vector<int> local_q;
+    std::vector<std::pair<int, long long>> outer_div;
 };
 
 // Whether a forward pass of this geometry uses the padded tile layout: runs
@@ -288,8 +296,8 @@ class Gen {
         const int NP = std::max(1, p_.params ? p_.npool : 1);
         const int NA = p_.T / p_.SEG;
         const size_t boff = ((size_t)NA * 8 + 15) & ~(size_t)15;
-        o_ << "struct __align__(16) A_" << name << " { C *psi; const P *gp; long long mode; long long geo[" << NG
-           << "]; P pool[" << NP << "]; };\n";
+        o_ << "struct __align__(16) A_" << name << " { C *psi; const P *gp; long long mode; double *rows; long long geo["
+           << NG << "]; P pool[" << NP << "]; };\n";
         o_ << "extern \"C\" __global__ void __launch_bounds__(" << p_.threads << ") " << name
            << "(const __grid_constant__ A_" << name << " A) {\n";
         o_ << "  extern __shared__ __align__(16) unsigned char qj_sm[];\n";
@@ -298,6 +306,7 @@ class Gen {
         o_ << "  C *buf1 = buf0 + " << p_.slots() << ";   // tile of " << p_.T << " amplitudes\n";
         o_ << "  const int tid = threadIdx.x;\n";
         emit_lanes();
+        if (p_.red) o_ << "  double qr_acc0 = 0.0, qr_acc1 = 0.0;\n";
         o_ << "  const bool db = A.mode != 0;\n";
         emit_offA(NA);
         o_ << "  __syncthreads();\n";
@@ -321,8 +330,94 @@ class Gen {
             else stage(st);
             o_ << "    __syncthreads();\n";
         }
+        if (p_.red) reduce_tile();
         transfer(false, {{"tile", "A.psi"}});
-        o_ << "    __syncthreads();\n  }\n  qj_wait0();\n}\n";
+        o_ << "    __syncthreads();\n  }\n  qj_wait0();\n";
+        if (p_.red) reduce_finish();
+        o_ << "}\n";
+    }
+
+    // <N_q> for every qudit and the norm of the finished tile (complex64),
+    // when A.rows is set.  Blocks of DK consecutive tile elements (the K2
+    // lowest local qudits, all in one run) give p = |psi|^2 sums in FP32 per
+    // thread: the norm, the K2 low qudits' digit-weighted sums (literal
+    // digits) and the other local qudits' sums (digit of the block); a warp's
+    // sums are added across lanes (shuffles), and lane c of each warp adds
+    // output c (and c + 32) of the tile to its FP64 accumulator: a local
+    // qudit's sum, an outer qudit's digit (from the tile index) times the
+    // norm, or the norm.
+    void reduce_tile() {
+        const int nt = p_.nt, rL = p_.T == p_.SEG ? nt : ipow_log(p_.SEG);
+        const int K2 = std::min(rL, D_ == 2 ? 4 : D_ == 3 ? 3 : 2);
+        const int DK = ipow_i(D_, K2), NB = p_.T / DK;
+        o_ << "    if (A.rows) {\n      float qr_P = 0.f";
+        for (int i = 0; i < nt; ++i) o_ << ", qr_S" << i << " = 0.f";
+        o_ << ";\n";
+        o_ << "      for (int blk = tid; blk < " << NB << "; blk += " << p_.threads << ") {\n";
+        o_ << "        const int e0 = blk * " << DK << ";\n";
+        if (p_.pad) {
+            o_ << "        const int ra = e0 / " << p_.SEG << ";\n";
+            o_ << "        const C *q = tile + e0 + ra + ((tp ^ ra) & 1);\n";
+        } else {
+            o_ << "        const C *q = tile + e0;\n";
+        }
+        o_ << "        float pb = 0.f";
+        for (int k = 0; k < K2; ++k) o_ << ", pk" << k << " = 0.f";
+        o_ << ";\n";
+        for (int r = 0; r < DK; ++r) {
+            o_ << "        { const C v = q[" << r << "]; const float pr = fmaf(v.x, v.x, v.y * v.y); pb += pr;";
+            for (int k = 0; k < K2; ++k) {
+                const int dig = (r / ipow_i(D_, K2 - 1 - k)) % D_;   // slot k = local position nt - K2 + k
+                if (dig == 1) o_ << " pk" << k << " += pr;";
+                else if (dig > 1) o_ << " pk" << k << " = fmaf(" << dig << ".f, pr, pk" << k << ");";
+            }
+            o_ << " }\n";
+        }
+        o_ << "        qr_P += pb;";
+        for (int k = 0; k < K2; ++k) o_ << " qr_S" << (nt - K2 + k) << " += pk" << k << ";";
+        o_ << "\n";
+        for (int i = 0; i < nt - K2; ++i) {
+            const int div = ipow_i(D_, nt - 1 - i) / DK;   // local stride / DK
+            o_ << "        qr_S" << i << " = fmaf((float)((blk / " << div << ") % " << D_ << "), pb, qr_S" << i << ");\n";
+        }
+        o_ << "      }\n";
+        // warp sums
+        o_ << "      for (int o = 16; o > 0; o >>= 1) { qr_P += __shfl_xor_sync(0xffffffffu, qr_P, o);";
+        for (int i = 0; i < nt; ++i) o_ << " qr_S" << i << " += __shfl_xor_sync(0xffffffffu, qr_S" << i << ", o);";
+        o_ << " }\n";
+        // each lane picks its outputs c = lane, lane + 32
+        o_ << "      const unsigned tt = (unsigned)t;\n";
+        for (int half = 0; half < 2; ++half) {
+            if (half == 1 && p_.n + 1 <= 32) break;
+            const std::string acc = half ? "qr_acc1" : "qr_acc0";
+            const int off = half * 32;
+            o_ << "      { double ad = 0.0; const int c = (tid & 31) + " << off << ";\n";
+            for (int i = 0; i < nt; ++i)
+                o_ << "        if (c == " << p_.local_q[i] << ") ad = (double)qr_S" << i << ";\n";
+            for (const auto &od : p_.outer_div)
+                o_ << "        if (c == " << od.first << ") ad = (double)((tt / " << od.second << "u) % " << D_
+                   << "u) * (double)qr_P;\n";
+            o_ << "        if (c == " << p_.n << ") ad = (double)qr_P;\n";
+            o_ << "        " << acc << " += ad; }\n";
+        }
+        o_ << "    }\n";
+    }
+
+    // Per-CTA rows: the warps' accumulators summed in warp order.
+    void reduce_finish() {
+        const int W = p_.threads / 32, C1 = p_.n + 1;
+        o_ << "  if (A.rows) {\n    double *qr_w = reinterpret_cast<double *>(qj_sm);\n    __syncthreads();\n";
+        o_ << "    if ((tid & 31) < " << std::min(C1, 32) << ") qr_w[(tid >> 5) * 64 + (tid & 31)] = qr_acc0;\n";
+        if (C1 > 32) o_ << "    if ((tid & 31) + 32 < " << C1 << ") qr_w[(tid >> 5) * 64 + 32 + (tid & 31)] = qr_acc1;\n";
+        o_ << "    __syncthreads();\n";
+        o_ << "    for (int c = tid; c < " << C1 << "; c += " << p_.threads << ") { double s = 0.0; for (int w = 0; w < "
+           << W << "; ++w) s += qr_w[w * 64 + c]; A.rows[(long long)blockIdx.x * " << C1 << " + c] = s; }\n  }\n";
+    }
+
+    int ipow_log(int x) const {
+        int e = 0;
+        for (int v = 1; v < x; v *= D_) ++e;
+        return e;
     }
 
     // Padded layout: run a of the tile fills the 16-byte aligned window of
@@ -871,6 +966,7 @@ struct JitPassInfo {
     size_t smem = 0;
     int grid = 1;
     bool params = true;     // pool in the kernel parameters
+    bool red = false;       // reduces <N_q> when given rows (the program's last pass, complex64)
     int npool = 0;
     size_t arg_bytes = 0, pool_off = 0;
     int NG = 1;
@@ -909,6 +1005,27 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.strideA.assign(pp.geom.strideA, pp.geom.strideA + pp.geom.kA);
         ps.adj = adj;
         ps.pad = use_pad(d, c128, adj, ps.SEG);
+        ps.n = 0;
+        for (long long N = 1; N < (long long)ps.ntiles * ps.T; N *= d) ++ps.n;
+        // the last pass of a complex64 forward program can reduce <N_q> too
+        if (!adj && !c128 && pi + 1 == plan.size() && ps.ntiles < (1ll << 32) && ps.n + 1 <= 64) {
+            ps.red = true;
+            const int n = ps.n;
+            for (int i = 0; i < ps.nt; ++i)
+                ps.local_q.push_back(i < ps.kA ? pp.active[i] : n - pp.geom.rL + (i - ps.kA));
+            long long prefix = 1;
+            for (int r = 0; r < ps.nruns; ++r) {
+                int hi = n - 1, len = 0;
+                for (long long v = ps.runS[r]; v > 1; v /= d) --hi;
+                for (long long v = ps.runM[r]; v > 1; v /= d) ++len;
+                long long dx = prefix;
+                for (int x = hi; x > hi - len; --x) {
+                    ps.outer_div.push_back({x, dx});
+                    dx *= d;
+                }
+                prefix *= ps.runM[r];
+            }
+        }
         ps.K = std::min(k_override > 0 ? k_override : (adj ? jit_stage_k_adj(d, c128) : jit_stage_k(d, c128, ps.df)),
                         pp.geom.nt);
         ps.ops = ops[pi];
@@ -967,7 +1084,8 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
             ji.l1_copies = !c128 && !ps.pad && !(d % 2 == 0 && ps.SEG % 2 == 0);
         }
         ji.ncols = ps.ncols;
-        ji.header = adj ? 40 : 24;
+        ji.header = adj ? 40 : 32;
+        ji.red = ps.red;
         ji.params = ps.params;
         ji.npool = npool;
         ji.NG = std::max(1, 2 * ps.nruns + ps.kA);
@@ -1182,20 +1300,22 @@ bool jit_pass_global_pool(const JitProgram *jp, size_t pi) { return !jp->passes[
 // (complex64: (re, re, -im, im) as float4; complex128: (re, im) as double2),
 // 16 bytes each; gpool is their device copy when the pass reads them globally.
 qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void *psi, const TileGeom &g,
-                     const void *prepared, int npool, const void *gpool) {
+                     const void *prepared, int npool, const void *gpool, double *rows) {
     const JitPassInfo &ji = jp->passes[pi];
     std::vector<unsigned char> args(ji.arg_bytes, 0);
     std::memcpy(args.data(), &psi, 8);
     std::memcpy(args.data() + 8, &gpool, 8);
     const long long mode = ji.dbuf ? 1 : 0;
     std::memcpy(args.data() + 16, &mode, 8);
+    if (!ji.red) rows = nullptr;
+    std::memcpy(args.data() + 24, &rows, 8);
     long long geo[2 * (kMaxActive + 1) + kMaxActive] = {};
     for (int r = 0; r < g.nruns; ++r) {
         geo[r] = g.runM[r];
         geo[g.nruns + r] = g.runS[r];
     }
     for (int i = 0; i < g.kA; ++i) geo[2 * g.nruns + i] = g.strideA[i];
-    std::memcpy(args.data() + 24, geo, 8 * (size_t)(2 * g.nruns + g.kA));
+    std::memcpy(args.data() + 32, geo, 8 * (size_t)(2 * g.nruns + g.kA));
     if (ji.params && npool > 0) std::memcpy(args.data() + ji.pool_off, prepared, 16 * (size_t)npool);
     void *kp[] = {args.data()};
     const CUresult r = g_drv.launch(ji.fn, (unsigned)ji.grid, 1, 1, (unsigned)ji.threads, 1, 1, (unsigned)ji.smem,
@@ -1203,6 +1323,8 @@ qf_status jit_launch(const JitProgram *jp, size_t pi, cudaStream_t stream, void 
     if (r != CUDA_SUCCESS) return set_error(QF_ERR_CUDA, "tile pass launch failed: " + cuda_err(r));
     return QF_OK;
 }
+
+bool jit_pass_reduces(const JitProgram *jp, size_t pi) { return jp && pi < jp->passes.size() && jp->passes[pi].red; }
 
 // Launches reverse pass pi of the adjoint sweep; rows receives grid x ncols
 // doubles (jit_pass_grid, jit_pass_ncols).

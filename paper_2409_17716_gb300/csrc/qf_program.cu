@@ -226,8 +226,11 @@ static std::vector<std::vector<TOp>> jit_ops(const qf_program *p, const double *
 }
 
 // Forward run with the passes compiled for this plan.
+// expect_out (device, n + 1 doubles, or nullptr): <N_q> and the norm of the
+// final state, reduced inside the last pass where that pass can (a compiled
+// complex64 tile pass), else by the separate reduction after it.
 template <typename R>
-static qf_status run_program_jit(qf_program *p, qf_state *s, const double *params) {
+static qf_status run_program_jit(qf_program *p, qf_state *s, const double *params, double *expect_out = nullptr) {
     using C = cplx<R>;
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
@@ -324,8 +327,13 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
             const void *gp = jit_pass_global_pool(p->jitp, pi)
                                  ? (const void *)(reinterpret_cast<const unsigned char *>(p->d_buf) + goff[pi])
                                  : nullptr;
+            double *rows = nullptr;
+            if (expect_out && pi + 1 == np && jit_pass_reduces(p->jitp, pi) &&
+                (size_t)jit_pass_grid(p->jitp, pi) * (n + 1) <=
+                    (size_t)reduce_max_blocks(s->num_sms) * (kMaxQudits + 1 + kMaxD))
+                rows = s->d_partials;
             qf_status st = jit_launch(p->jitp, pi, s->stream, psi, pp.geom, prep[pi].data(),
-                                      (int)(prep[pi].size() / 16), gp);
+                                      (int)(prep[pi].size() / 16), gp, rows);
             if (st != QF_OK) return st;
         }
         ++launched;
@@ -336,10 +344,22 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
             p->tafter.push_back(cur);
             prev_ev = cur;
         }
+        if (expect_out && pi + 1 == np && !pp.strided && !pp.mc && jit_pass_reduces(p->jitp, pi) &&
+            (size_t)jit_pass_grid(p->jitp, pi) * (n + 1) <=
+                (size_t)reduce_max_blocks(s->num_sms) * (kMaxQudits + 1 + kMaxD)) {
+            // the pass's per-CTA rows -> <N_q> and the norm (outside the pass timing)
+            cudaError_t e = launch_sum_rows(s->stream, s->d_partials, jit_pass_grid(p->jitp, pi), n + 1, expect_out);
+            if (e != cudaSuccess) return cuda_error(e, "fused <N_q> row sums");
+            expect_out = nullptr;   // done
+        }
     }
     if (packed) {
         qf_status cst = convert(false);
         if (cst != QF_OK) return cst;
+    }
+    if (expect_out) {   // not fused into the last pass
+        cudaError_t e = launch_expect_number<R>(L, psi, d, n, s->d_partials, expect_out);
+        if (e != cudaSuccess) return cuda_error(e, "<N_q> reduction");
     }
     QF_CUDA(cudaEventRecord(p->done_ev, s->stream));
     p->ran = true;
@@ -348,7 +368,7 @@ static qf_status run_program_jit(qf_program *p, qf_state *s, const double *param
 }
 
 template <typename R>
-static qf_status run_program_t(qf_program *p, qf_state *s, const double *params) {
+static qf_status run_program_t(qf_program *p, qf_state *s, const double *params, double *expect_out = nullptr) {
     using C = cplx<R>;
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
@@ -358,7 +378,7 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params)
         p->plan_c128 = c128;
         drop_jit(p);
     }
-    if (p->jit) return run_program_jit<R>(p, s, params);
+    if (p->jit) return run_program_jit<R>(p, s, params, expect_out);
     // resolve every pass; tile passes get their op list + pool in one buffer
     struct Built {
         bool strided = false, mc = false;
@@ -1230,6 +1250,28 @@ qf_status qf_program_run(qf_program *p, qf_state *s, const double *params) {
     }
     if (p->mixed) return mixed_program_run(p, s, params);
     return s->dt == QF_C64 ? run_program_t<float>(p, s, params) : run_program_t<double>(p, s, params);
+}
+
+qf_status qf_program_run_expect(qf_program *p, qf_state *s, const double *params, double *out_dev) {
+    if (!out_dev || ((uintptr_t)out_dev & 7) != 0)
+        return set_error(QF_ERR_ARG, "qf_program_run_expect: output must be a non-NULL 8-byte aligned device pointer");
+    if (!p || !s) return set_error(QF_ERR_ARG, "program or state is NULL");
+    if (!same_dims(p, s)) return set_error(QF_ERR_ARG, "program and state sizes differ");
+    if (p->num_params > 0 && !params) return set_error(QF_ERR_ARG, "program needs parameters");
+    if (p->mixed || p->gates.empty() || !p->jit) {
+        qf_status st = qf_program_run(p, s, params);
+        if (st != QF_OK) return st;
+        qf_obs obs = {QF_OBS_NUMBER_ALL, 0, nullptr};
+        return qf_expect_device(s, &obs, out_dev);
+    }
+    if (!p->up_ev) {
+        if (cudaEventCreateWithFlags(&p->up_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QF_ERR_CUDA, "event creation failed");
+        }
+    }
+    return s->dt == QF_C64 ? run_program_t<float>(p, s, params, out_dev) : run_program_t<double>(p, s, params, out_dev);
 }
 
 qf_status qf_program_plan(qf_program *p, qf_dtype dt, int *num_passes, int *num_strided, int *max_ops) {

@@ -84,6 +84,7 @@ _PROTOS = {
     "qf_program_add_mcu": (_int, [_vp, _c.POINTER(_int), _c.POINTER(_int), _int, _int, _c.POINTER(_dbl)]),
     "qf_program_set_fusion": (_int, [_vp, _int]),
     "qf_program_set_fp64": (_int, [_vp, _int]),
+    "qf_program_run_expect": (_int, [_vp, _vp, _vp, _vp]),
     "qf_state_upload": (_int, [_vp, _vp, _c.c_longlong, _c.c_longlong]),
     "qf_host_alloc": (_int, [_c.c_size_t, _c.POINTER(_vp)]),
     "qf_host_free": (_int, [_vp]),
@@ -526,6 +527,17 @@ def qf_program_run(p: int, s: int, params=None) -> None:
     else:
         a = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
         _call("qf_program_run", p, s, _dptr(a))
+
+
+def qf_program_run_expect(p: int, s: int, out_dev_ptr: int, params=None) -> None:
+    """Runs the program and writes <N_q> (q < n) and the norm to the device
+    buffer at out_dev_ptr (n + 1 FP64 values), fused into the last pass
+    where it can be."""
+    if params is None:
+        _call("qf_program_run_expect", p, s, None, out_dev_ptr)
+    else:
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+        _call("qf_program_run_expect", p, s, _dptr(a), out_dev_ptr)
 
 
 def _f64(a):
