@@ -551,35 +551,45 @@ def c128_throughput(qf, W, torch, sizes, hbm_peak, rates):
 
 
 def per_gate_sweep(qf, W, torch, hbm_peak):
-    """Single-gate GB/s of each gate kind at every target position, d=3 n=17,
-    complex64 (strided kernel for stride >= 32, tile kernel below)."""
+    """Single-gate GB/s of each gate kind at every target position, all four
+    sizes, complex64 and complex128 (immediate mode: the strided kernel at
+    every stride).  Algorithmic bytes count the level rows a gate changes;
+    effective bytes count whole 32-byte sectors -- below a sector per row
+    the untouched rows share sectors with the touched ones, so the whole
+    state moves."""
     import numpy as np
-    d, n = 3, 17
-    N = d ** n
-    b = 8
-    st = qf.State(d, n, "c64").set_basis(0)
-    rng = np.random.default_rng(7)
-    U = W.haar_unitary(d, rng)
-    kinds = {
-        "dense(H/Haar)": (lambda q: qf.qf_apply_gate(st.handle, [q], U), 2 * N * b),
-        "rot_pair(RY 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "y"), 2 * N * b * 2 / d),
-        "diag(clock Z)": (lambda q: qf.qf_apply_z(st.handle, q, 1), 2 * N * b * (d - 1) / d),
-        "rz_pair(RZ 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "z"), 2 * N * b * 2 / d),
-        "shift(X)": (lambda q: qf.qf_apply_x(st.handle, q, 1), 2 * N * b),
-        "sum(c=q-1,t=q)": (lambda q: qf.qf_apply_sum(st.handle, (q - 1) % n, q), 2 * N * b * (d - 1) / d),
-    }
     out = {}
-    for name, (fn, by) in kinds.items():
-        rows = []
-        for q in range(n):
-            fn(q)
-            ms = _time_ms(torch, lambda: fn(q), reps=5)
-            rows.append(by / (ms / 1e3) / 1e9)
-        wide = [r for q, r in enumerate(rows) if d ** (n - 1 - q) >= 32]
-        out[name] = {"gbps_by_target": [round(r, 1) for r in rows], "median_gbps": statistics.median(rows),
-                     "median_frac": statistics.median(rows) / hbm_peak,
-                     "median_frac_wide": (statistics.median(wide) / hbm_peak) if wide else None}
-    st.free()
+    for dtype, b in (("c64", 8), ("c128", 16)):
+        for d, n in SIZES:
+            N = d ** n
+            st = qf.State(d, n, dtype).set_basis(0)
+            U = W.haar_unitary(d, np.random.default_rng(7))
+            kinds = {
+                "dense(H/Haar)": (lambda q: qf.qf_apply_gate(st.handle, [q], U), 1.0),
+                "rot_pair(RY 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "y"), 2 / d),
+                "diag(clock Z)": (lambda q: qf.qf_apply_z(st.handle, q, 1), (d - 1) / d),
+                "rz_pair(RZ 0,1)": (lambda q: qf.qf_apply_rot(st.handle, q, 0, 1, 0.7, "z"), 2 / d),
+                "shift(X)": (lambda q: qf.qf_apply_x(st.handle, q, 1), 1.0),
+                "sum(c=q-1,t=q)": (lambda q: qf.qf_apply_sum(st.handle, (q - 1) % n, q), (d - 1) / d),
+            }
+            rec = {}
+            for name, (fn, frac) in kinds.items():
+                alg, eff = [], []
+                for q in range(n):
+                    S = d ** (n - 1 - q)
+                    fn(q)
+                    ms = _time_ms(torch, lambda: fn(q), reps=5)
+                    alg_b = 2 * N * b * frac
+                    eff_b = alg_b if S * b >= 32 else 2 * N * b
+                    alg.append(alg_b / (ms / 1e3) / 1e9)
+                    eff.append(eff_b / (ms / 1e3) / 1e9)
+                rec[name] = {"gbps_by_target": [round(x, 1) for x in alg],
+                             "median_frac": statistics.median(alg) / hbm_peak,
+                             "min_frac_effective": min(eff) / hbm_peak,
+                             "median_frac_effective": statistics.median(eff) / hbm_peak}
+            out["d%d_n%d_%s" % (d, n, dtype)] = rec
+            st.free()
+            torch.cuda.empty_cache()
     return out
 
 
