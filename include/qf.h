@@ -319,8 +319,10 @@ qf_status qf_program_set_fusion(qf_program *p, int enable);
  * state's).  exact = 1 computes in FP64 (on GB300 about 1/70 of the FP32
  * rate).  In the double-float form amplitudes must stay below 2^128 in
  * magnitude; parts of magnitude 2^-74 .. 2^-126 keep an absolute precision of
- * 2^-96 and smaller ones become 0.  The adjoint sweep and the
- * immediate-mode gates always use FP64. */
+ * 2^-96 and smaller ones become 0.  The same choice applies to the compiled
+ * reverse passes of the adjoint sweep (psi and lambda converted around them;
+ * gradient terms summed in double-float per block, then in FP64); lambda =
+ * O psi, the loss and the immediate-mode gates use FP64. */
 qf_status qf_program_set_fp64(qf_program *p, int exact);
 /* qf_program_run followed by <N_q> of every qudit and the norm ("Code
  * style": measure returns the marginals; <N_q> = sum_m m P_q(m)) into out_dev

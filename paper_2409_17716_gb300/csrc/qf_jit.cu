@@ -195,6 +195,32 @@ __device__ __forceinline__ C jn(C a) {
     qts(qf2(a.x, a.y), qf2(a.z, a.w), s, t);
     return make_float4(s.x, s.y, t.x, t.y);
 }
+// Gradient terms of the adjoint sweep as double-float reals (hi, lo):
+// Im(conj(l) g) = lr gi - li gr from one paired TwoProduct and a TwoSum.
+__device__ __forceinline__ void qts1(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ float2 qim(C l, C g) {
+    float2 p, e;
+    qtp(qf2(l.x, l.y), qf2(l.z, l.w), qf2(g.y, g.x), qf2(g.w, g.z), p, e);
+    float s, t;
+    qts1(p.x, -p.y, s, t);
+    return qf2(s, t + (e.x - e.y));
+}
+__device__ __forceinline__ float2 qad(float2 a, float2 b) {
+    float s, t;
+    qts1(a.x, b.x, s, t);
+    return qf2(s, a.y + b.y + t);
+}
+// a * (mh + ml): a double-float real times a double-float entry
+__device__ __forceinline__ float2 qmu(float2 a, float mh, float ml) {
+    const float p = a.x * mh;
+    const float e = fmaf(a.x, mh, -p) + fmaf(a.x, ml, a.y * mh);
+    return qf2(p, e);
+}
+__device__ __forceinline__ double qdd(float2 a) { return (double)a.x + (double)a.y; }
 #define QJ_CP_BYTES "16"
 #define QJ_CP_KIND "cg"
 #else
@@ -685,7 +711,84 @@ class Gen {
     }
 
     // Adds the block's Im <lambda|G|psi> of a parametrised op to g<gcol>.
+    // Double-float form of grad(): the block's terms summed as double-float
+    // reals (qim / qad / qmu), added to the FP64 column once per op and block.
+    void grad_df(const TOp &o) {
+        const int sa = o.q[4], sc = o.q[5];
+        const int gm = o.gmat;
+        const bool ctrl = is_controlled(o);
+        const std::string gv = "g" + std::to_string(o.gcol);
+        auto scaled = [&](const std::string &x, int cl) {
+            return cl == 1 ? x : "qmu(" + x + ", " + std::to_string(cl) + ".f, 0.f)";
+        };
+        if (o.kind == OP_PAIR || o.kind == OP_CPAIR) {
+            const int RS = rs(sa);
+            auto fib = [&](int b0, int cl) {
+                const std::string a = Pv(b0 + o.j * RS), c = Pv(b0 + o.k * RS);
+                const std::string la = W(b0 + o.j * RS), lc = W(b0 + o.k * RS);
+                o_ << "      { const C ga = jma(" << E(gm + 1) << ", " << c << ", jm(" << E(gm) << ", " << a
+                   << ")); const C gc = jma(" << E(gm + 3) << ", " << c << ", jm(" << E(gm + 2) << ", " << a << ")); "
+                   << "qt = qad(qt, " << scaled("qad(qim(" + la + ", ga), qim(" + lc + ", gc))", cl) << "); }\n";
+            };
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { float2 qt = qf2(0.f, 0.f);\n";
+                for (int b0 : fibres(sa)) fib(b0, 1);
+                o_ << "      " << gv << " += qdd(qmu(qt, (float)cl, 0.f)); } }\n";
+                return;
+            }
+            o_ << "      { float2 qt = qf2(0.f, 0.f);\n";
+            for (int b0 : fibres(sa)) {
+                const int cl = ctrl ? slot_digit(b0, sc) : 1;
+                if (cl == 0) continue;
+                fib(b0, cl);
+            }
+            o_ << "      " << gv << " += qdd(qt); }\n";
+            return;
+        }
+        if (o.kind == OP_DIAG || o.kind == OP_CDIAG) {
+            if (sa < 0) {
+                const int DK = ipow_i(D_, p_.K);
+                o_ << "      { const int dg = " << outside_digit(o.lsa) << "; if ((" << o.mask
+                   << " >> dg) & 1) { float2 qt = qf2(0.f, 0.f);";
+                for (int r = 0; r < DK; ++r) o_ << " qt = qad(qt, qim(" << W(r) << ", " << Pv(r) << "));";
+                o_ << " const P ge = " << Edyn(std::to_string(gm) + " + dg") << "; " << gv
+                   << " += qdd(qmu(qt, ge.h.x, ge.l.x)); } }\n";
+                return;
+            }
+            const int RS = rs(sa);
+            auto fib = [&](int b0) {
+                for (int l = 0; l < D_; ++l)
+                    if ((o.mask >> l) & 1)
+                        o_ << "      qt = qad(qt, qmu(qim(" << W(b0 + l * RS) << ", " << Pv(b0 + l * RS) << "), " << E(gm + l)
+                           << ".h.x, " << E(gm + l) << ".l.x));\n";
+            };
+            if (ctrl && sc < 0) {
+                o_ << "      { const int cl = " << outside_digit(o.lsc) << "; if (cl) { float2 qt = qf2(0.f, 0.f);\n";
+                for (int b0 : fibres(sa)) fib(b0);
+                o_ << "      " << gv << " += qdd(qmu(qt, (float)cl, 0.f)); } }\n";
+                return;
+            }
+            o_ << "      { float2 qt = qf2(0.f, 0.f);\n";
+            for (int b0 : fibres(sa)) {
+                const int cl = ctrl ? slot_digit(b0, sc) : 1;
+                if (cl == 0) continue;
+                if (cl == 1) {
+                    fib(b0);
+                } else {
+                    o_ << "      { float2 qs = qt; qt = qf2(0.f, 0.f);\n";
+                    fib(b0);
+                    o_ << "      qt = qad(qs, qmu(qt, " << cl << ".f, 0.f)); }\n";
+                }
+            }
+            o_ << "      " << gv << " += qdd(qt); }\n";
+        }
+    }
+
     void grad(const TOp &o) {
+        if (p_.df) {
+            grad_df(o);
+            return;
+        }
         const int sa = o.q[4], sc = o.q[5];
         const int gm = o.gmat;
         const bool ctrl = is_controlled(o);
@@ -993,7 +1096,7 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         PassSrc &ps = specs[pi];
         ps.d = d;
         ps.c128 = c128;
-        ps.df = df && c128 && !adj;
+        ps.df = df && c128;
         ps.T = pp.geom.T;
         ps.SEG = pp.geom.SEG;
         ps.nt = pp.geom.nt;

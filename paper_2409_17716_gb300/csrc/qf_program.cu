@@ -31,6 +31,7 @@ struct qf_program {
     bool fp64 = false;                 // complex128 compiled passes in FP64 (default: double-float)
     JitProgram *jitadj = nullptr;      // compiled reverse passes of `adj_plan`
     bool jitadj_c128 = false;
+    bool jitadj_df = false;
     int tile_qudits = 0, min_run_qudits = 0, max_ops = 0;   // planner overrides (0: default)
     bool plan_valid = false;
     bool plan_c128 = false;
@@ -495,7 +496,8 @@ static qf_status run_program_t(qf_program *p, qf_state *s, const double *params,
 // op.gcol.  With `prep`, also the prepared entries of every pass.
 template <typename R>
 static std::vector<std::vector<TOp>> adj_jit_ops(const qf_program *p, const std::vector<PassPlan> &exec,
-                                                 const double *params, std::vector<std::vector<unsigned char>> *prep) {
+                                                 const double *params, std::vector<std::vector<unsigned char>> *prep,
+                                                 bool df = false) {
     std::vector<std::vector<TOp>> ops(exec.size());
     if (prep) prep->assign(exec.size(), std::vector<unsigned char>());
     for (size_t k = 0; k < exec.size(); ++k) {
@@ -508,7 +510,10 @@ static std::vector<std::vector<TOp>> adj_jit_ops(const qf_program *p, const std:
             TOp o = localize(r.op, pp.geom, pp.active, p->n, p->d);
             o.mat = off;
             off += (int)r.m.size();
-            if (prep) append_prepared<R>(r, (*prep)[k]);
+            if (prep) {
+                if (df) append_prepared_df(r, (*prep)[k]);
+                else append_prepared<R>(r, (*prep)[k]);
+            }
             o.gcol = -1;
             o.gmat = 0;
             const HGate &g0 = p->gates[grp[0]];
@@ -518,7 +523,10 @@ static std::vector<std::vector<TOp>> adj_jit_ops(const qf_program *p, const std:
                 ROp gen;
                 gen.m = generator_entries(g0, p->d);
                 off += (int)gen.m.size();
-                if (prep) append_prepared<R>(gen, (*prep)[k]);
+                if (prep) {
+                    if (df) append_prepared_df(gen, (*prep)[k]);
+                    else append_prepared<R>(gen, (*prep)[k]);
+                }
             }
             ops[k].push_back(o);
         }
@@ -535,19 +543,21 @@ static qf_status run_adjoint_jit(qf_program *p, qf_state *psi, qf_state *lam, co
     const int d = p->d, n = p->n;
     const bool c128 = sizeof(R) == 8;
     const int np = (int)p->adj_plan.size();
+    const bool df = c128 && !p->fp64;   // double-float reverse passes (see run_program_jit)
     std::vector<PassPlan> exec(p->adj_plan.rbegin(), p->adj_plan.rend());
-    if (!p->jitadj || p->jitadj_c128 != c128) {
+    if (!p->jitadj || p->jitadj_c128 != c128 || p->jitadj_df != df) {
         if (p->jitadj) {
             jit_free(p->jitadj);
             p->jitadj = nullptr;
         }
-        std::vector<std::vector<TOp>> ops = adj_jit_ops<R>(p, exec, params, nullptr);
-        qf_status st = jit_build(exec, ops, d, c128, p->jit_k, true, psi->num_sms, &p->jitadj);
+        std::vector<std::vector<TOp>> ops = adj_jit_ops<R>(p, exec, params, nullptr, df);
+        qf_status st = jit_build(exec, ops, d, c128, p->jit_k, true, psi->num_sms, &p->jitadj, df);
         if (st != QF_OK) return st;
         p->jitadj_c128 = c128;
+        p->jitadj_df = df;
     }
     std::vector<std::vector<unsigned char>> prep;
-    adj_jit_ops<R>(p, exec, params, &prep);
+    adj_jit_ops<R>(p, exec, params, &prep, df);
     // gradient rows and terms: (rows base, CTAs, columns, column) per slot, in execution order
     std::vector<long long> rows_base(np, 0);
     std::vector<std::vector<std::array<long long, 4>>> terms(p->num_params);
@@ -620,8 +630,20 @@ static qf_status run_adjoint_jit(qf_program *p, qf_state *psi, qf_state *lam, co
     if (e != cudaSuccess) return cuda_error(e, "lambda = O psi");
     const unsigned char *dev = reinterpret_cast<const unsigned char *>(p->d_buf);
     const MixedShape ushape = uniform_shape(d, n);
+    const long long N = ipow_ll(d, n);
+    bool packed = false;
+    auto convert = [&](bool pack) -> cudaError_t {
+        cudaError_t ce = launch_df_convert(psi->stream, psi->num_sms, psi->data, N, pack);
+        if (ce == cudaSuccess) ce = launch_df_convert(psi->stream, psi->num_sms, lam->data, N, pack);
+        packed = pack;
+        return ce;
+    };
     for (int k = 0; k < np; ++k) {
         const PassPlan &pp = exec[k];
+        if (df && packed != !pp.mc) {
+            e = convert(!pp.mc);
+            if (e != cudaSuccess) return cuda_error(e, "double-float conversion");
+        }
         if (pp.mc) {
             const ROp &r = single[k];
             std::vector<C> m(r.m.size());
@@ -637,6 +659,10 @@ static qf_status run_adjoint_jit(qf_program *p, qf_state *psi, qf_state *lam, co
         st = jit_launch_adj(p->jitadj, k, psi->stream, ps, ls, p->d_rows + rows_base[k], pp.geom, prep[k].data(),
                             (int)(prep[k].size() / 16), gp);
         if (st != QF_OK) return st;
+    }
+    if (packed) {
+        e = convert(false);
+        if (e != cudaSuccess) return cuda_error(e, "double-float conversion");
     }
     e = launch_grad_gather(L, p->d_rows, dev + terms_off, reinterpret_cast<const int *>(dev + first_off), p->num_params,
                            grad_dev);
@@ -1178,7 +1204,7 @@ qf_status qf_program_jit_source(qf_program *p, qf_dtype dt, int adjoint, char *b
         std::vector<PassPlan> exec(p->adj_plan.rbegin(), p->adj_plan.rend());
         std::vector<std::vector<TOp>> ops = c128 ? adj_jit_ops<double>(p, exec, zeros.data(), nullptr)
                                                  : adj_jit_ops<float>(p, exec, zeros.data(), nullptr);
-        st = jit_source(exec, ops, p->d, c128, p->jit_k, true, &src);
+        st = jit_source(exec, ops, p->d, c128, p->jit_k, true, &src, c128 && !p->fp64);
     } else {
         if (!p->plan_valid || p->plan_c128 != c128) {
             p->plan = plan_passes(p->gates, p->d, p->n, c128, p->fuse, false, p->tile_qudits, p->max_ops,

@@ -61,7 +61,9 @@ def test_rz_only_zero_gradient(orc):
     ops += [W.Op("rot", (q,), j=2, axis="g", param=2 * n + q) for q in range(n)]
     psi0 = orc.basis(d, n, 37)
     _, g, _ = gradient(qf, ops, d, n, np.linspace(0.1, 1.0, 3 * n), np.ones(n), psi0=psi0)
-    assert np.abs(g).max() < 1e-15
+    # exactly zero in exact arithmetic; rounding of the complex128 sweep
+    # (double-float passes: about 2^-48 relative) leaves a few 1e-15
+    assert np.abs(g).max() < 1e-13
 
 
 def mixed_circuit(d, n, seed):

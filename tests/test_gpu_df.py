@@ -104,3 +104,34 @@ def test_multicontrolled_between_compiled_passes(orc):
     want = orc.run(ops, d, n, psi0)
     got = _run(qf, ops, d, n, psi0, False)
     assert np.abs(got - want).max() <= 1e-12
+
+
+@pytest.mark.parametrize("d,n", [(3, 5), (2, 8), (5, 3), (4, 4)])
+def test_adjoint_double_float_vs_fp64_and_oracle(orc, d, n):
+    """The complex128 adjoint sweep with double-float reverse passes (default)
+    and with FP64: gradients within 1e-10 of the oracle's derivative circuits,
+    losses within 1e-12, psi restored to |0...0>."""
+    qf = gpu_lib()
+    ops, P = W.variational_ansatz(d, n, 3)
+    ops = [W.Op("h", (q,)) for q in range(n)] + ops
+    ops += [W.Op("crot", (0, n - 1), j=0, k=1, axis="y", param=0), W.Op("crot", (n - 1, 1), j=0, k=1, axis="z", param=1),
+            W.Op("rot", (1,), j=d - 1, axis="g", param=2), W.Op("crot", (1, 0), j=1, axis="g", param=3),
+            W.Op("swap", (0, 1))]
+    theta = W.normal_angles(P, seed=d + n)
+    w = np.linspace(0.5, 1.5, n)
+    want = orc.grad_bruteforce(ops, d, n, theta, w)
+    want_l = orc.loss(orc.run(ops, d, n, params=theta), d, n, w)
+    for exact in (False, True):
+        p = qf.program_from_ops(d, n, ops)
+        qf.qf_program_set_fp64(p, exact)
+        psi, lam = qf.State(d, n, "c128").set_basis(0), qf.State(d, n, "c128")
+        loss, g = qf.qf_program_gradient(p, psi.handle, lam.handle, theta, w)
+        back = download(psi)
+        assert abs(loss - want_l) <= 1e-12, (exact, loss, want_l)
+        assert np.abs(g - want).max() <= 1e-10, (exact, np.abs(g - want).max())
+        e0 = np.zeros_like(back)
+        e0[0] = 1.0
+        assert np.abs(back - e0).max() <= 1e-12
+        qf.qf_program_free(p)
+        psi.free()
+        lam.free()
