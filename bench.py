@@ -428,14 +428,15 @@ def main():
             "gpu_launches": launches, "clocks": clocks, "roofline": roofline}
 
     if extras:
-        line["per_size"] = per_size_throughput(qf, W, torch, sizes, states, progs, args)
+        line["per_size"] = per_size_throughput(qf, W, torch, sizes, states, progs, args, hbm_peak)
+        line["roofline"]["frac_by_d"] = {str(r["d"]): r["hbm_frac"] for r in line["per_size"]}
+        line["e2e"] = e2e_throughput(qf, W, torch, sizes, progs, args)
         line["unfused"] = unfused_throughput(qf, W, torch, sizes, states, circ)
         rates = qf.qf_device_fma_rates()
         line["alu_peaks"] = {"fp64_fma_tflops": 2 * rates[0] / 1e12, "fp32_fma_tflops": 2 * rates[1] / 1e12,
                              "how": "qf_device_fma_rates: independent FMA chains, CUDA events, best of 5"}
         line["c128"] = c128_throughput(qf, W, torch, sizes, hbm_peak, rates)
         line["per_gate"] = per_gate_sweep(qf, W, torch, hbm_peak)
-        line["e2e"] = e2e_throughput(qf, W, torch, sizes, progs, args)
     for p in progs:
         qf.qf_program_free(p)
     for st in states:
@@ -495,12 +496,16 @@ def forward_outputs(qf, W, torch, d=3, n=17):
     return out
 
 
-def per_size_throughput(qf, W, torch, sizes, states, progs, args):
+def per_size_throughput(qf, W, torch, sizes, states, progs, args, hbm_peak):
+    """Each size's program alone: time, rate, and the HBM fraction of its
+    passes (pass count x 2 N b over the program time)."""
     out = []
     for (d, n), st, p in zip(sizes, states, progs):
         ms = _time_ms(torch, lambda: qf.qf_program_run(p, st.handle), reps=5)
-        out.append({"d": d, "n": n, "amps": d ** n, "passes": qf.qf_program_last_passes(p),
-                    "ms": ms, "au_per_s": d ** n * N_GATES / (ms / 1e3)})
+        passes = qf.qf_program_last_passes(p)
+        out.append({"d": d, "n": n, "amps": d ** n, "passes": passes,
+                    "ms": ms, "au_per_s": d ** n * N_GATES / (ms / 1e3),
+                    "hbm_frac": passes * 2 * d ** n * 8 / (ms / 1e3) / 1e9 / hbm_peak})
     return out
 
 

@@ -17,13 +17,15 @@ size:
   the complex64 and complex128 losses against each other; the complex128
   adjoint gradient against FP64 central differences (h = 1e-5) of the
   complex128 forward (itself oracle-pinned at the benchmark sizes and by the
-  product circuit above) on a subset of parameters spread over all layers,
-  relative error <= 1e-6; the complex64 adjoint gradient against the same
+  product circuit above) on 32 parameters spread over all layers, relative
+  error <= 1e-6; the complex64 adjoint gradient against the same
   differences (its error is stated, and bounded loosely).
 
 The differences reuse prefixes: one complex128 state advances through the
 circuit, and at each chosen parameter a copy runs the remaining gates at
-theta +- h, so the subset costs about (K + 1) forward passes instead of 2K.
+theta +- h, so K parameters cost about K + 1 forward runs instead of 2K
+(the complex128 forward runs in double-float arithmetic, about 1.7 s at this
+size).
 """
 import numpy as np
 import pytest
@@ -35,9 +37,9 @@ from paper_2409_17716_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 D, NQ, LAYERS = 3, 20, 4
-# parameters checked by finite differences: every layer, every rotation kind
-# and qudits across the register (slot = layer*80 + kind*20 + qudit)
-FD_SLOTS = [0, 47, 94, 141, 188, 235, 282, 319]
+# 32 parameters checked by finite differences: every layer, every rotation
+# kind and qudits across the register (slot = layer*80 + kind*20 + qudit)
+FD_SLOTS = sorted({(10 * i + 7 * (i % 4)) % 320 for i in range(32)} | {0, 319})[:32]
 
 
 def _need(torch, gbytes):
