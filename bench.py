@@ -582,6 +582,8 @@ def per_gate_sweep(qf, W, torch, hbm_peak):
                 alg, eff = [], []
                 for q in range(n):
                     S = d ** (n - 1 - q)
+                    if name.startswith("sum"):   # skips the control-0 blocks: the control's stride counts too
+                        S = min(S, d ** (n - 1 - (q - 1) % n))
                     fn(q)
                     ms = _time_ms(torch, lambda: fn(q), reps=5)
                     alg_b = 2 * N * b * frac

@@ -332,7 +332,10 @@ class Gen {
         o_ << "  C *buf1 = buf0 + " << p_.slots() << ";   // tile of " << p_.T << " amplitudes\n";
         o_ << "  const int tid = threadIdx.x;\n";
         emit_lanes();
-        if (p_.red) o_ << "  double qr_acc0 = 0.0, qr_acc1 = 0.0;\n";
+        if (p_.red) {
+            o_ << "  double qr_acc0 = 0.0, qr_acc1 = 0.0;\n";
+            reduce_roles();
+        }
         o_ << "  const bool db = A.mode != 0;\n";
         emit_offA(NA);
         o_ << "  __syncthreads();\n";
@@ -411,22 +414,36 @@ class Gen {
         o_ << "      for (int o = 16; o > 0; o >>= 1) { qr_P += __shfl_xor_sync(0xffffffffu, qr_P, o);";
         for (int i = 0; i < nt; ++i) o_ << " qr_S" << i << " += __shfl_xor_sync(0xffffffffu, qr_S" << i << ", o);";
         o_ << " }\n";
-        // each lane picks its outputs c = lane, lane + 32
+        // each lane adds its outputs c = lane, lane + 32: a local qudit's sum
+        // (selected by literal compares), an outer qudit's digit of the tile
+        // index (the lane's divisor, set once per kernel) times the norm, or
+        // the norm -- formed in FP32, one conversion to FP64 per output
         o_ << "      const unsigned tt = (unsigned)t;\n";
         for (int half = 0; half < 2; ++half) {
             if (half == 1 && p_.n + 1 <= 32) break;
             const std::string acc = half ? "qr_acc1" : "qr_acc0";
+            const std::string dv = half ? "qr_div1" : "qr_div0";
             const int off = half * 32;
-            o_ << "      { double ad = 0.0; const int c = (tid & 31) + " << off << ";\n";
-            for (int i = 0; i < nt; ++i)
-                o_ << "        if (c == " << p_.local_q[i] << ") ad = (double)qr_S" << i << ";\n";
-            for (const auto &od : p_.outer_div)
-                o_ << "        if (c == " << od.first << ") ad = (double)((tt / " << od.second << "u) % " << D_
-                   << "u) * (double)qr_P;\n";
-            o_ << "        if (c == " << p_.n << ") ad = (double)qr_P;\n";
-            o_ << "        " << acc << " += ad; }\n";
+            o_ << "      { float ad = 0.f; const int c = (tid & 31) + " << off << ";\n";
+            for (int i = 0; i < nt; ++i) o_ << "        if (c == " << p_.local_q[i] << ") ad = qr_S" << i << ";\n";
+            o_ << "        if (" << dv << ") ad = qr_P * (float)((tt / " << dv << ") % " << D_ << "u);\n";
+            o_ << "        if (c == " << p_.n << ") ad = qr_P;\n";
+            o_ << "        " << acc << " += (double)ad; }\n";
         }
         o_ << "    }\n";
+    }
+
+    // Once per kernel: the tile-index divisor of each lane's outer-qudit
+    // outputs (0 for local qudits and the norm).
+    void reduce_roles() {
+        for (int half = 0; half < 2; ++half) {
+            const std::string dv = half ? "qr_div1" : "qr_div0";
+            o_ << "  unsigned " << dv << " = 0u;\n";
+            if (half == 1 && p_.n + 1 <= 32) continue;
+            o_ << "  { const int c = (threadIdx.x & 31) + " << half * 32 << ";";
+            for (const auto &od : p_.outer_div) o_ << " if (c == " << od.first << ") " << dv << " = " << od.second << "u;";
+            o_ << " }\n";
+        }
     }
 
     // Per-CTA rows: the warps' accumulators summed in warp order.
