@@ -932,6 +932,9 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
     torch.cuda.synchronize()
     steps = max(3, args.steps // 2)
     per_step, copy_ms = [], []
+    import gc
+    gc.collect()
+    gc.disable()   # a full collection of the process's objects is a host pause, not library time
     t0 = time.perf_counter()
     for _ in range(steps):
         ts = time.perf_counter()
@@ -940,6 +943,7 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
         copy_ms.append(sum(a.elapsed_time(b) for a, b in ev))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    gc.enable()
     assert all(abs(r[-1] - 1.0) < 1e-3 for r in res)
     for st in states:
         st.free()
