@@ -919,19 +919,31 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
     states = [qf.State(d, n, "c64", stream=s) for (d, n), s in zip(sizes, streams)]
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sizes]
 
+    calls = []   # host wall time of every library call of the last step
+
     def step():
+        calls.clear()
         for i, (st, (ptr, count)) in enumerate(zip(states, host)):
             ev[i][0].record(streams[i])
+            t = time.perf_counter()
             qf.qf_state_upload(st.handle, ptr, 0, count)
+            calls.append(("upload", i, time.perf_counter() - t))
             ev[i][1].record(streams[i])
+            t = time.perf_counter()
             qf.qf_program_run(progs[i], st.handle)
-        return [qf.qf_expect(st.handle, qf.QF_OBS_NUMBER_ALL) for st in states]
+            calls.append(("run", i, time.perf_counter() - t))
+        out = []
+        for i, st in enumerate(states):
+            t = time.perf_counter()
+            out.append(qf.qf_expect(st.handle, qf.QF_OBS_NUMBER_ALL))
+            calls.append(("expect", i, time.perf_counter() - t))
+        return out
 
     for _ in range(2):
         step()
     torch.cuda.synchronize()
     steps = max(3, args.steps // 2)
-    per_step, copy_ms = [], []
+    per_step, copy_ms, step_calls = [], [], []
     import gc
     gc.collect()
     gc.disable()   # a full collection of the process's objects is a host pause, not library time
@@ -941,6 +953,7 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
         res = step()
         per_step.append(1e3 * (time.perf_counter() - ts))
         copy_ms.append(sum(a.elapsed_time(b) for a, b in ev))
+        step_calls.append([(c, i, round(1e3 * x, 2)) for c, i, x in calls])
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     gc.enable()
@@ -957,6 +970,9 @@ def e2e_throughput(qf, W, torch, sizes, progs, args):
             "h2d_gbs_in_step_median": bytes_in / (sorted(copy_ms)[len(copy_ms) // 2] / 1e3) / 1e9,
             "step_ms": {"min": min(per_step), "median": med, "max": max(per_step)},
             "step_ms_each": [round(x, 2) for x in per_step],
+            # host wall ms of each call (kind, state) in the slowest and in the median step
+            "calls_slowest_step": step_calls[per_step.index(max(per_step))],
+            "calls_median_step": step_calls[per_step.index(med)],
             "value_at_median_step": au / steps / (med / 1e3),
             "note": "per state (own stream, smallest first): qf_state_upload from page-locked host memory "
                     "(qf_host_alloc), qf_program_run, qf_expect to the host"}

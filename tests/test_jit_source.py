@@ -3,6 +3,7 @@ with NVRTC for sm_103a (host only, no GPU): every gate kind, controls inside
 and outside a register stage, shared-memory SWAP and multi-qudit gates,
 complex64 and complex128, default and overridden stage slots."""
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -171,3 +172,50 @@ def test_benchmark_passes_compile_without_spills(d, n):
         assert rc == 0, log[:2000]
         spills = [int(x) for x in re.findall(r"(\d+) bytes spill stores", log)]
         assert spills and max(spills) <= 16, log[-600:]
+
+
+def test_direct_stages():
+    """Forward passes whose first (complex64, odd d) or last register stage
+    holds only active qudits read or write HBM directly from the stage's
+    registers: the source says so in its stage summary, such a pass has no
+    tile copy on that side, and the global offsets of a direct stage's
+    registers are the active strides' digit sums.  The pass that reduces
+    <N_q> keeps its shared-memory tile; complex128 passes store directly
+    but load through shared memory."""
+    import re
+    L = _nvrtc()
+    d, n = 3, 17
+    p = qf.program_from_ops(d, n, W.random_circuit(d, n, 200))
+    units = _units(p, qf.QF_C64)
+    tags = [re.search(r"// register stages: ([^\n]*)", u).group(1) for u in units]
+    assert any("first from HBM" in t for t in tags) and any("last to HBM" in t for t in tags)
+    assert "HBM" not in tags[-1]   # the reducing pass
+    for u, t in zip(units, tags):
+        if "first from HBM" in t:
+            assert "for (; t <" in u and "qj_cp2(" not in u.split("for (; t <")[1]
+            # run-number digit 0 first, as the offA table composes them
+            strides = [int(x) for x in re.findall(r"o \+= \(long long\)\(rem % 3\) \* (\d+)LL", u)]
+            seg = int(re.search(r"const int gab = b / (\d+);", u).group(1))
+            first = u.split("for (int blk = tid; blk <")[1]
+            ins = [int(x) for x in re.findall(r"const int q = b / (\d+); b = q \*", first.split("C v0")[0])]
+            offs = [int(x) for x in re.findall(r"C v\d+ = gq\[(\d+)LL\];", first)]
+            # slot strides, most significant first, as run-number digits
+            digs = sorted((round(math.log(s // seg, 3)) for s in ins), reverse=True)
+            want = []
+            for r in range(d ** len(digs)):
+                g = 0
+                for i, dg in enumerate(digs):
+                    g += ((r // d ** (len(digs) - 1 - i)) % d) * strides[dg]
+                want.append(g)
+            assert offs == want, (offs, want)
+        if "last to HBM" in t:
+            assert "qj_st2(A.psi" not in u and "A.psi[g" not in u
+    for u in units[:3]:
+        rc, log = _compile(L, u)
+        assert rc == 0, log[:2000]
+    c128 = _units(p, qf.QF_C128)
+    ct = [re.search(r"// register stages: ([^\n]*)", u).group(1) for u in c128]
+    assert any("last to HBM" in t for t in ct) and not any("first from HBM" in t for t in ct)
+    rc, log = _compile(L, next(u for u, t in zip(c128, ct) if "last to HBM" in t))
+    assert rc == 0, log[:2000]
+    qf.qf_program_free(p)
