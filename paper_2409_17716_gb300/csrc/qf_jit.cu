@@ -305,6 +305,7 @@ struct PassSrc {
     // an active qudit (its registers then sit in whole runs: consecutive
     // threads read consecutive amplitudes of a run).
     bool din = false, dout = false;
+    bool pf = false;   // L2 prefetch of the next tile (forward complex64 passes at odd d)
     std::vector<std::pair<int, long long>> outer_div;
 };
 
@@ -370,6 +371,10 @@ class Gen {
             o_ << "      qj_commit();\n      qj_wait0();\n    }\n";
             o_ << "    __syncthreads();\n";
         }
+        // the prefetch goes between the first two stages (barriers keep its
+        // registers apart from the stages'), before the only stage otherwise
+        const bool pf_first = p_.pf && p_.stages.size() < 2;
+        if (pf_first) prefetch_next(name);
         if (p_.pad) o_ << "    const int tp = (int)(base & 1);\n";
         for (size_t si = 0; si < p_.stages.size(); ++si) {
             const TStage &st = p_.stages[si];
@@ -377,12 +382,29 @@ class Gen {
             if (st.legacy) legacy(p_.ops[st.first]);
             else stage(st, si == 0 && p_.din, last && p_.dout);
             if (!(last && p_.dout)) o_ << "    __syncthreads();\n";
+            if (si == 0 && p_.pf && !pf_first) prefetch_next(name);
         }
         if (p_.red) reduce_tile();
         if (!p_.dout) transfer(false, {{"tile", "A.psi"}});
         o_ << "    __syncthreads();\n  }\n  qj_wait0();\n";
         if (p_.red) reduce_finish();
         o_ << "}\n";
+    }
+
+    // Without a double buffer, the CTA's next tile is fetched into L2 while
+    // this one is processed: every 128-byte line of each of its runs (the
+    // run's last byte too, for runs that start inside a line), so its tile
+    // copy or direct loads find the lines in L2 instead of waiting on HBM.
+    void prefetch_next(const std::string &name) {
+        const int NA = p_.T / p_.SEG;
+        const long long RB = (long long)p_.SEG * (long long)elt();   // bytes of a run
+        const long long LPR = (RB + 127) / 128 + 1;
+        o_ << "    if (!db) { const long long tn = t + gridDim.x;\n      if (tn < " << p_.ntiles
+           << ") { const long long bn = qj_tb_" << name << "(tn);\n";
+        o_ << "        for (int k = tid; k < " << NA * LPR << "; k += " << p_.threads << ") { const int a = k / " << LPR
+           << "; const long long l = (long long)(k - a * " << LPR << ") * 128; "
+           << "const char *pl = reinterpret_cast<const char *>(A.psi + bn + offA[a]) + (l < " << RB << " ? l : " << RB - 1
+           << "); asm volatile(\"prefetch.L2 [%0];\" :: \"l\"(pl)); }\n      }\n    }\n";
     }
 
     // <N_q> for every qudit and the norm of the finished tile (complex64),
@@ -1214,15 +1236,17 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
         ps.ops = ops[pi];
         ps.stages = build_stages(ps.ops, pp.geom, d, ps.K);
         ops[pi] = ps.ops;   // the stage slots written by build_stages
-        // Direct stages (forward passes, not the reducing pass, whose tile
-        // goes through shared memory for the reduction): the last stage
-        // stores to HBM at every d and precision; the first stage loads from
-        // HBM for complex64 at odd d.  Measured on GB300 (200-gate programs,
-        // program time): complex64 d=2 6.01 -> 5.94 ms, d=3 6.71 -> 6.26,
-        // d=4 9.52 -> 9.39, d=5 18.82 -> 17.45; complex128 (double-float)
-        // 2 % faster.  Direct loads at even d lose the double-buffered
-        // prefetch (d=2 2 %, d=4 4 % slower), and in double-float passes
-        // they measured 1.3 % slower than direct stores alone.
+        // Direct stages (forward and adjoint passes, not the reducing pass,
+        // whose tile goes through shared memory for the reduction): the last
+        // stage stores to HBM at every d and precision; the first stage loads
+        // from HBM for complex64 at odd d.  Measured on GB300 (200-gate
+        // programs, program time): complex64 d=2 6.01 -> 5.94 ms, d=3 6.71 ->
+        // 6.26, d=4 9.52 -> 9.39, d=5 18.82 -> 17.45; complex128 (double-
+        // float) 2 % faster; adjoint gradients (d=3 ansatz) 4.50 -> 4.31 ms
+        // at n=14, 1559 -> 1485 ms at n=20 (complex64), 16.6 -> 16.3 ms
+        // (complex128).  Direct loads at even d lose the double-buffered
+        // prefetch (d=2 2 %, d=4 4 % slower), and in double-float passes they
+        // measured 1.3 % slower than direct stores alone.
         if (!ps.red && !ps.stages.empty() && ps.T > ps.SEG) {
             auto direct = [&](const TStage &s) {
                 if (s.legacy) return false;
@@ -1232,12 +1256,14 @@ static std::vector<std::string> gen_sources(const std::vector<PassPlan> &plan, s
             };
             ps.din = !c128 && d % 2 == 1 && direct(ps.stages.front());
             ps.dout = direct(ps.stages.back());
-            if (adj) {
-                const char *e1 = getenv("QF_JIT_ADJ_DIN"), *e2 = getenv("QF_JIT_ADJ_DOUT");
-                ps.din = ps.din && e1 && atoi(e1);
-                ps.dout = ps.dout && e2 && atoi(e2);
-            }
         }
+        // L2 prefetch of the next tile: complex64 forward passes at odd d
+        // (never double-buffered) whose runs are at least a cache line.
+        // Measured per pass on GB300: runs of 27-729 amplitudes up to 12 %
+        // faster (d=3 program 6.27 -> 5.97 ms), 25-amplitude runs 0-6 %;
+        // 5-amplitude (40-byte) runs 4-51 % slower (two prefetches and an
+        // index per 40 bytes, and up to 17 more registers).
+        ps.pf = !adj && !c128 && d % 2 == 1 && (long long)ps.SEG * 8 >= 128;
         int npool = 0;
         bool dense_k = false;
         for (const TOp &o : ps.ops) dense_k |= o.kind == OP_DENSEK;
