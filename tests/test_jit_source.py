@@ -219,3 +219,33 @@ def test_direct_stages():
     rc, log = _compile(L, next(u for u, t in zip(c128, ct) if "last to HBM" in t))
     assert rc == 0, log[:2000]
     qf.qf_program_free(p)
+
+
+@pytest.mark.parametrize("d,n,dtype,adjoint", [(3, 12, qf.QF_C64, False), (5, 8, qf.QF_C64, True), (7, 6, qf.QF_C64, False),
+                                               (4, 8, qf.QF_C128, False), (3, 10, qf.QF_C128, True)])
+def test_direct_stage_variants_compile(d, n, dtype, adjoint):
+    """Direct stages and the L2 prefetch in other shapes: odd and even d,
+    d = 7, forward and adjoint, complex64 and complex128 (double-float), with
+    shared-memory SWAPs between register stages; every unit with a direct
+    stage compiles.  The prefetch appears only in complex64 forward passes at
+    odd d whose runs are at least 128 bytes."""
+    import re
+    L = _nvrtc()
+    ops = W.random_circuit(d, n, 50) + [W.Op("swap", (0, n - 1))] + W.random_circuit(d, n, 30, seed=7)
+    if adjoint:
+        ops, _ = W.variational_ansatz(d, n, 2, entangler="chain")
+    p = qf.program_from_ops(d, n, ops)
+    src = qf.qf_program_jit_source(p, dtype, adjoint=adjoint)
+    units = [u for u in src.split("// ---- translation unit\n") if u.strip()]
+    direct = [u for u in units if "HBM" in re.search(r"// register stages: ([^\n]*)", u).group(1)]
+    assert direct
+    for u in direct[:3]:
+        rc, log = _compile(L, u)
+        assert rc == 0, log[:2000]
+        if "first from HBM" in u:
+            assert dtype == qf.QF_C64 and d % 2 == 1
+    for u in units:
+        if "prefetch.L2" in u:
+            seg = int(re.search(r"tile of (\d+)", u).group(1)) // int(re.search(r"for \(int a = tid; a < (\d+);", u).group(1))
+            assert dtype == qf.QF_C64 and not adjoint and d % 2 == 1 and seg * 8 >= 128
+    qf.qf_program_free(p)
