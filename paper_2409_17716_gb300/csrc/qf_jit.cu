@@ -322,9 +322,12 @@ class Gen {
     // Forward pass.  With A.mode != 0 tiles are double-buffered: while a CTA
     // applies the gates to one tile, the copy of its next tile is in flight,
     // so the barrier after a tile's load rarely waits on HBM; the host picks
-    // that mode only where the second buffer costs no CTAs per SM.  The tile
-    // geometry is literal (tile bases by division by constants in every
-    // thread).  Shared memory: run offsets, then one or two tiles.
+    // that mode only where the second buffer costs no CTAs per SM.  A pass
+    // with a direct first stage has no tile load (its first stage reads HBM),
+    // one with a direct last stage no tile store; single-buffered passes with
+    // long runs prefetch their next tile into L2 instead.  The tile geometry
+    // is literal (tile bases by division by constants in every thread).
+    // Shared memory: run offsets, then one or two tiles.
     void kernel(const std::string &name) {
         const int NG = std::max(1, 2 * p_.nruns + p_.kA);
         const int NP = std::max(1, p_.params ? p_.npool : 1);
